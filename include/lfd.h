@@ -1,0 +1,227 @@
+/*
+ * lfd.h - C ABI of the GB300 (sm_103a) subpixel-level 3D Gaussian Splatting
+ * renderer for lenticular light-field displays (CoherentRaster,
+ * arXiv 2605.04509).
+ *
+ * The renderer takes a set of 3D Gaussians, the cameras of the display's
+ * view cone and the panel's lenticular parameters, and writes the interlaced
+ * light-field image I_LF in R^{W x H x 3} (Sec. 4, problem statement;
+ * Alg. 1 inputs and output). Every step runs in CUDA kernels of this library.
+ *
+ * General rules
+ *  - Device pointers are CUDA device (or managed) addresses valid on the
+ *    current device; host pointers are ordinary CPU memory. The caller owns
+ *    every buffer it passes; no call frees or retains caller memory beyond
+ *    its own duration. A plan owns its panel tables and its scratch memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream). Rendering calls enqueue work on it; they block the host once per
+ *    frame to read back the pair count P (needed to size the pair buffers),
+ *    and again only when stage timing or evaluation counting is enabled.
+ *  - A plan may be used by one host thread at a time; frames rendered with
+ *    one plan on one stream are ordered. Different plans are independent.
+ *  - Return value: LFD_OK (0) or a negative LFD_ERR_* code. No call aborts,
+ *    traps or throws. lfd_status_string() gives the text; after
+ *    LFD_ERR_CUDA, lfd_last_error() gives the CUDA error message of the
+ *    calling thread's last failure.
+ *
+ * Layouts (row-major, float32 unless stated)
+ *  - Gaussians (Sec. 3.3): means [M][3]; scales [M][3] (activated, > 0);
+ *    quats [M][4] in (w, x, y, z) order (normalised inside); opacities [M]
+ *    (activated, in [0, 1]); sh [M][(d+1)^2][3] real SH coefficients of
+ *    degree d <= 3 in the 3DGS basis.
+ *  - Camera: world->camera rotation R (row-major 3x3), translation t,
+ *    pinhole fx, fy, cx, cy in pixels (x right, y down, z forward). Every
+ *    view renders at panel resolution.
+ *  - Image: out_rgb [H][W][3]; subpixel (x, y, u) at (y*W + x)*3 + u; values
+ *    are not clamped.
+ *  - Clusters (Appendix B.1): C = views_per_cluster, K = ceil(N / C); slot l
+ *    of cluster k is view min(k*C + l, N-1); the representative is slot
+ *    floor(C/2).
+ *  - Projected attributes (Eq. 5-6), for k in [0, K), i in [0, M):
+ *      means2d       [K][M][C][2]  2D mean of Gaussian i in the view of slot
+ *                                  l; NaN where the Gaussian lies at or in
+ *                                  front of the near plane z = 0.2 of that
+ *                                  view (culled there)
+ *      conic_opacity [K][M][4]     (a, b, c, o): inverse of the 2D covariance
+ *                                  [[a, b], [b, c]] at the representative
+ *                                  view, and the opacity o
+ *      color_tau     [K][M][4]     (r, g, b, tau): SH colour at the
+ *                                  representative view, and
+ *                                  tau = 2 ln(255 o) (the region q <= tau is
+ *                                  where alpha >= 1/255); tau < 0 marks a
+ *                                  Gaussian culled for the whole cluster
+ *      depth         [K][M]        view-space depth at the representative
+ */
+#ifndef LFD_H
+#define LFD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LFD_API __attribute__((visibility("default")))
+#else
+#define LFD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LFD_OK 0
+#define LFD_ERR_INVALID (-1)  /* bad argument, size or combination           */
+#define LFD_ERR_OOM (-2)      /* device allocation failed                    */
+#define LFD_ERR_CAPACITY (-3) /* pair count or key width beyond the limits   */
+#define LFD_ERR_CUDA (-4)     /* a CUDA call failed; see lfd_last_error()    */
+#define LFD_ERR_STATE (-5)    /* the requested data does not exist (yet)     */
+
+/* Key-generation and sort strategy. Both produce the identical sorted list
+ * and range table.
+ *  LFD_SORT_DEPTH_FIRST: sort the K*M per-cluster depths once, emit the
+ *    Gaussian-tile pairs in that order and sort them stably by the
+ *    (tile, cluster) bits only.
+ *  LFD_SORT_KEY64: emit the 64-bit keys of Eq. 11 in (k, i) order and sort
+ *    them stably over their 32 + Bit_K + Bit_T used bits. */
+#define LFD_SORT_DEPTH_FIRST 0
+#define LFD_SORT_KEY64 1
+
+/* lfd_set_flags() bits */
+#define LFD_FLAG_STAGE_TIMING 1 /* fill lfd_stats.ms_* (adds host syncs)  */
+#define LFD_FLAG_COUNT_EVALS 2  /* fill lfd_stats.num_evals              */
+
+typedef struct lfd_plan lfd_plan;
+
+/* Lenticular panel (Sec. 3.1): resolution W x H, N views (1..255), tan of
+ * the grating tilt angle alpha, grating pitch L_x in subpixels (> 0) and the
+ * lens-to-panel offset K_offset in subpixels. */
+typedef struct {
+  int32_t width, height, num_views;
+  double tan_slant, pitch, k_offset;
+} lfd_panel;
+
+/* Rendering options. tile_w * tile_h <= 512, both in [4, 64]; C in
+ * [1, 32]; remap must be 1 (view-coherent remap, Sec. 4.3); sort_mode one of
+ * LFD_SORT_*; bg is the background colour added as T * bg. */
+typedef struct {
+  int32_t tile_w, tile_h;
+  int32_t views_per_cluster;
+  int32_t remap;
+  int32_t sort_mode;
+  float bg[3];
+} lfd_opts;
+
+typedef struct {
+  const float *means, *scales, *quats, *opacities, *sh; /* device */
+  int64_t count;
+  int32_t sh_degree;
+} lfd_gaussians;
+
+typedef struct {
+  float R[9], t[3], fx, fy, cx, cy;
+} lfd_camera;
+
+typedef struct {
+  int32_t num_clusters;   /* K */
+  int32_t tiles_x, tiles_y;
+  int32_t tile_capacity;  /* 3 * tile_w * tile_h */
+  int32_t bit_k, bit_t;   /* ceil(log2 K), ceil(log2 T) */
+  int32_t max_segment;    /* largest (tile, cluster) subpixel run */
+} lfd_plan_info;
+
+typedef struct {
+  int64_t num_pairs;  /* P: Gaussian-(tile, cluster) pairs of the last frame */
+  int64_t num_evals;  /* E: list entries visited by all subpixels (flag)    */
+  float ms_project, ms_keygen, ms_sort, ms_blend; /* stage times (flag)    */
+} lfd_stats;
+
+/* Create a plan for one panel and option set on the current device: builds
+ * the view index matrix V (Eq. 1-3, FP64 arithmetic), the per-tile
+ * view-sorted subpixel table Psi (Sec. 4.3, Eq. 8; "precomputed once since
+ * the lens geometry is fixed") and the per-(tile, cluster) runs inside it.
+ * Synchronous. *out receives the plan, or NULL on error. */
+LFD_API int lfd_plan_create(const lfd_panel *panel, const lfd_opts *opts, lfd_plan **out);
+
+/* Release a plan and all device memory it owns (synchronises the device). */
+LFD_API void lfd_plan_destroy(lfd_plan *plan);
+
+LFD_API int lfd_plan_get_info(const lfd_plan *plan, lfd_plan_info *out);
+
+/* Enable LFD_FLAG_* bits for the following frames. */
+LFD_API int lfd_set_flags(lfd_plan *plan, int32_t flags);
+
+/* Copy the panel tables to host memory (each pointer may be NULL):
+ *   V      uint8 [H][W][3]  view index per subpixel (Eq. 3)
+ *   psi    uint16 [T][3*TW*TH]  per tile, the tile's in-panel subpixels as
+ *          local row-major indices (yl*TW + xl)*3 + u, stably sorted by view
+ *          (Eq. 8); entries past n_sub[t] are unspecified
+ *   n_sub  int32 [T]        in-panel subpixels of each tile
+ *   seg    int32 [T][K+1]   first psi position of each cluster's run */
+LFD_API int lfd_plan_copy_tables(const lfd_plan *plan, uint8_t *V, uint16_t *psi,
+                         int32_t *n_sub, int32_t *seg);
+
+/* Projection with cross-view attribute reuse (Sec. 4.2, Eq. 5-6; Alg. 1
+ * stage 1): per-view 2D means for every slot of every cluster, and the
+ * covariance, depth and SH colour of each cluster's representative view.
+ * cams: host array of num_cams == N cameras. Outputs are caller-owned device
+ * buffers in the layouts above. Asynchronous on stream. */
+LFD_API int lfd_project(lfd_plan *plan, const lfd_gaussians *g, const lfd_camera *cams,
+                int32_t num_cams, float *means2d, float *conic_opacity,
+                float *color_tau, float *depth, void *stream);
+
+/* Key generation, sort, range identification and subpixel blending
+ * (Sec. 4.2-4.3, Alg. 1 stages 2-4, Alg. 2) from projected attributes in the
+ * layouts above, for M Gaussians. Writes out_rgb [H][W][3] (device). A tile
+ * of cluster k holds Gaussian i when some view of the cluster's region
+ * {q <= tau} contains a pixel centre of the tile. Returns LFD_ERR_CAPACITY
+ * (output untouched) when P would exceed 2^32 - 1. stats may be NULL. */
+LFD_API int lfd_render_projected(lfd_plan *plan, int64_t M, const float *means2d,
+                         const float *conic_opacity, const float *color_tau,
+                         const float *depth, float *out_rgb, void *stream,
+                         lfd_stats *stats);
+
+/* The whole path (Alg. 1): lfd_project into plan-owned buffers, then
+ * lfd_render_projected. */
+LFD_API int lfd_render(lfd_plan *plan, const lfd_gaussians *g, const lfd_camera *cams,
+               int32_t num_cams, float *out_rgb, void *stream, lfd_stats *stats);
+
+/* End-to-end variant for callers holding HOST buffers: the Gaussians in g
+ * and out_rgb are host pointers (pinned memory gives the fastest copies). The
+ * call copies the inputs to plan-owned device memory, renders, copies the
+ * image back and returns once it is in out_rgb. */
+LFD_API int lfd_render_host(lfd_plan *plan, const lfd_gaussians *g_host,
+                    const lfd_camera *cams, int32_t num_cams, float *out_rgb_host,
+                    void *stream, lfd_stats *stats);
+
+/* Copy the last frame's sorted Gaussian list L (uint32 [P], Gaussian ids),
+ * range table (uint32 [T][K][2] = [S, E), (0, 0) when empty) and, with
+ * LFD_SORT_KEY64 only, the sorted Eq. 11 keys (uint64 [P]) to host memory.
+ * Any pointer may be NULL; capacity is the element count of list/keys.
+ * Synchronises the plan's last stream. LFD_ERR_STATE before the first frame
+ * or when keys are requested in depth-first mode. */
+LFD_API int lfd_plan_copy_lists(const lfd_plan *plan, uint32_t *list, uint32_t *ranges,
+                        uint64_t *keys, int64_t capacity);
+
+/* Stage times accumulated over frames rendered with LFD_FLAG_STAGE_TIMING,
+ * measured with CUDA events on each frame's stream and folded in without
+ * extra synchronisation (a frame's events are read at the next frame's
+ * pair-count read-back, or here). Synchronises the plan's last stream. */
+typedef struct {
+  int64_t frames;
+  double ms_project, ms_keygen, ms_sort, ms_blend; /* sums over frames */
+} lfd_stage_times;
+
+LFD_API int lfd_get_stage_totals(lfd_plan *plan, lfd_stage_times *out, int32_t reset);
+
+/* Number of CUDA kernels this library has launched in the process so far. */
+LFD_API uint64_t lfd_kernel_launches(void);
+
+LFD_API const char *lfd_status_string(int status);
+LFD_API const char *lfd_last_error(void);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+LFD_API int lfd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LFD_H */

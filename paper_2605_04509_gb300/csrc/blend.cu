@@ -1,0 +1,177 @@
+// Subpixel alpha blending with view-coherent remapping (Sec. 4.3, Eq. 9-10;
+// Alg. 2 Alpha-Blend; 3DGS rules: alpha = min(0.99, o exp(-q/2)), skip
+// alpha < 1/255, stop before a Gaussian that would take T below 1e-4).
+//
+// Work unit: one (tile t, cluster k) run of the remap table Psi. Because Psi
+// sorts each tile's subpixels by view, the subpixels of cluster k form one
+// contiguous run and all of them walk the same list [S_tk, E_tk). One CTA
+// owns one run: the list is staged in shared memory in batches of blockDim
+// Gaussians (conic pre-scaled by log2(e), opacity, colour, and the 2D means
+// of every slot view of the cluster), and each thread blends its subpixels
+// against the staged batch; a block-wide vote ends the walk once every
+// subpixel has saturated. Grid order is cluster-major so that one cluster's
+// attributes stay resident in L2 while its tiles are blended.
+#include "lfd_internal.h"
+
+namespace lfd {
+namespace {
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTMin = 1e-4f;
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+template <int R, bool COUNT>
+__global__ void __launch_bounds__(256) k_blend(PanelGeom g, BlendArgs a) {
+  extern __shared__ float4 smem[];
+  const int NB = blockDim.x;
+  float4* s_co = smem;
+  float4* s_col = smem + NB;
+  float2* s_mean = reinterpret_cast<float2*>(smem + 2 * NB);
+
+  const int k = blockIdx.x / g.T;
+  const int t = blockIdx.x - k * g.T;
+  const int s0 = a.seg[(size_t)t * (g.K + 1) + k];
+  const int n = a.seg[(size_t)t * (g.K + 1) + k + 1] - s0;
+  if (n <= 0) return;
+  const uint2 rg = a.ranges[(size_t)t * g.K + k];
+  const int tx = t % g.TX, ty = t / g.TX;
+
+  float px[R], py[R], T[R], acc[R];
+  int slot[R], ch[R];
+  int64_t oidx[R];
+  bool act[R];
+  uint32_t cnt = 0;
+#pragma unroll
+  for (int m = 0; m < R; ++m) {
+    const int r = threadIdx.x + m * NB;
+    act[m] = r < n;
+    T[m] = 1.f;
+    acc[m] = 0.f;
+    px[m] = py[m] = 0.f;
+    slot[m] = 0;
+    ch[m] = 0;
+    oidx[m] = 0;
+    if (act[m]) {
+      const uint32_t e = a.psi[(size_t)t * g.cap + s0 + r];
+      const int view = (int)(e >> 16);
+      const int loc = (int)(e & 0xffffu);
+      const int u = loc % 3;
+      const int xl = (loc / 3) % g.TW;
+      const int yl = (loc / 3) / g.TW;
+      const int x = tx * g.TW + xl, y = ty * g.TH + yl;
+      px[m] = (float)x + 0.5f;
+      py[m] = (float)y + 0.5f;
+      slot[m] = view - k * g.C;
+      ch[m] = u;
+      oidx[m] = ((int64_t)y * g.W + x) * 3 + u;
+    }
+  }
+  bool live[R];
+#pragma unroll
+  for (int m = 0; m < R; ++m) live[m] = act[m];
+
+  for (uint32_t base = rg.x; base < rg.y; base += (uint32_t)NB) {
+    bool any = false;
+#pragma unroll
+    for (int m = 0; m < R; ++m) any |= act[m];
+    if (!__syncthreads_or(any)) break;
+    const uint32_t e = base + threadIdx.x;
+    if (e < rg.y) {
+      const uint32_t gid = a.list[e];
+      const size_t rec = (size_t)k * a.M + gid;
+      const float4 co = reinterpret_cast<const float4*>(a.conic_opacity)[rec];
+      s_co[threadIdx.x] = make_float4(-0.5f * kLog2e * co.x, -kLog2e * co.y, -0.5f * kLog2e * co.z, co.w);
+      s_col[threadIdx.x] = reinterpret_cast<const float4*>(a.color_tau)[rec];
+      const float2* mp = reinterpret_cast<const float2*>(a.means2d) + rec * g.C;
+      for (int l = 0; l < g.C; ++l) s_mean[threadIdx.x * g.C + l] = mp[l];
+    }
+    __syncthreads();
+    const int nbatch = (int)min((uint32_t)NB, rg.y - base);
+    for (int gi = 0; gi < nbatch; ++gi) {
+      const float4 co = s_co[gi];
+      const float4 cl = s_col[gi];
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        if (!act[m]) continue;
+        if (COUNT) ++cnt;
+        const float2 mu = s_mean[gi * g.C + slot[m]];
+        const float dx = px[m] - mu.x;
+        const float dy = py[m] - mu.y;
+        const float power = co.x * dx * dx + co.z * dy * dy + co.y * dx * dy;
+        if (power > 0.f) continue;
+        const float v = co.w * ex2_approx(power);
+        if (!(v >= kAlphaMin)) continue;
+        const float alpha = fminf(kAlphaMax, v);
+        const float Tn = T[m] * (1.f - alpha);
+        if (Tn < kTMin) {
+          act[m] = false;
+          continue;
+        }
+        const float c = ch[m] == 0 ? cl.x : (ch[m] == 1 ? cl.y : cl.z);
+        acc[m] += c * alpha * T[m];
+        T[m] = Tn;
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < R; ++m) {
+    if (!live[m]) continue;
+    const float bg = ch[m] == 0 ? a.bg[0] : (ch[m] == 1 ? a.bg[1] : a.bg[2]);
+    a.out[oidx[m]] = acc[m] + T[m] * bg;
+  }
+  if (COUNT) {
+    unsigned long long c = cnt;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(a.eval_counter, c);
+  }
+}
+
+template <int R>
+cudaError_t launch_r(const PanelGeom& g, const BlendArgs& a, int block, cudaStream_t s) {
+  const size_t smem = (size_t)block * (2 * sizeof(float4) + g.C * sizeof(float2));
+  const unsigned grid = (unsigned)((int64_t)g.K * g.T);
+  if (a.eval_counter) {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_blend<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_blend<R, true><<<grid, block, smem, s>>>(g, a);
+    note_launches(1);
+  } else {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_blend<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_blend<R, false><<<grid, block, smem, s>>>(g, a);
+    note_launches(1);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_blend(const PanelGeom& g, const BlendArgs& a, cudaStream_t s) {
+  if ((int64_t)g.K * g.T == 0) return cudaSuccess;
+  const int need = a.max_segment > 0 ? a.max_segment : 1;
+  int R = 1;
+  while (R < 8 && (need + R - 1) / R > 256) R *= 2;
+  int block = (need + R - 1) / R;
+  block = ((block + 31) / 32) * 32;
+  if (block > 256) return cudaErrorInvalidValue;
+  switch (R) {
+    case 1:
+      return launch_r<1>(g, a, block, s);
+    case 2:
+      return launch_r<2>(g, a, block, s);
+    case 4:
+      return launch_r<4>(g, a, block, s);
+    default:
+      return launch_r<8>(g, a, block, s);
+  }
+}
+
+}  // namespace lfd

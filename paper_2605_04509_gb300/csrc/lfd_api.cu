@@ -1,0 +1,625 @@
+// C ABI of the renderer (include/lfd.h): plan management and the per-frame
+// orchestration of Alg. 1 (projection, key generation, sort, blend).
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <atomic>
+#include <new>
+
+#include "lfd_internal.h"
+
+using namespace lfd;
+
+namespace lfd {
+namespace {
+std::atomic<unsigned long long> g_launches{0};
+}
+void note_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+uint64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace lfd
+
+namespace {
+
+thread_local char g_last_error[512] = "";
+
+int fail_cuda(cudaError_t e, const char* where) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", where, cudaGetErrorName(e),
+           cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? LFD_ERR_OOM : LFD_ERR_CUDA;
+}
+
+int fail(int code, const char* msg) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s", msg);
+  return code;
+}
+
+#define LFD_CUDA(call)                                \
+  do {                                                \
+    cudaError_t e__ = (call);                         \
+    if (e__ != cudaSuccess) return fail_cuda(e__, #call); \
+  } while (0)
+
+int ceil_log2(uint64_t v) {
+  int b = 0;
+  while ((1ull << b) < v) ++b;
+  return b;
+}
+
+// A growable device buffer. Growth frees and reallocates (with headroom),
+// which synchronises the device; steady-state frames allocate nothing.
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  int ensure(size_t bytes) {
+    if (bytes <= cap) return LFD_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    const size_t want = bytes + bytes / 4 + 1024;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return fail_cuda(e, "cudaMalloc");
+    }
+    cap = want;
+    return LFD_OK;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+  template <typename T>
+  T* as() const {
+    return reinterpret_cast<T*>(p);
+  }
+};
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+}  // namespace
+
+struct lfd_plan {
+  lfd_panel panel;
+  lfd_opts opts;
+  PanelGeom g;
+  int device = 0;
+  int flags = 0;
+  int max_segment = 0;
+  // panel tables
+  uint8_t* V = nullptr;
+  uint32_t* psi = nullptr;
+  int32_t* n_sub = nullptr;
+  int32_t* seg = nullptr;
+  // per-frame scratch
+  DevBuf proj_means, proj_co, proj_ct, proj_depth;
+  DevBuf item_key[2], item_val[2];
+  DevBuf counts, offsets, scan_tmp;
+  DevBuf pair_key[2], pair_val[2];
+  DevBuf radix_tmp;
+  DevBuf ranges;
+  DevBuf small;  // [0] total pairs, [1] eval counter
+  DevBuf host_in[5];  // device copies of host Gaussians (lfd_render_host)
+  DevBuf image;       // device image for lfd_render_host
+  unsigned long long* h_small = nullptr;  // pinned
+  // last frame
+  int64_t last_P = -1;
+  int last_key_buf = 0;
+  int last_val_buf = 0;
+  int last_sort_mode = 0;
+  cudaStream_t last_stream = nullptr;
+  // stage-timing events, two sets used alternately: [0] frame start, [1]
+  // projection done, [2] key generation done, [3] sort + ranges done, [4]
+  // blend done. A set's times are folded into acc_ms at the next frame's
+  // pair-count synchronisation (when they are complete), or on request.
+  cudaEvent_t ev[2][5] = {};
+  int ev_set = 0;
+  bool ev_pending[2] = {false, false};
+  bool ev_has_project[2] = {false, false};
+  double acc_ms[4] = {0, 0, 0, 0};
+  int64_t acc_frames = 0;
+};
+
+namespace {
+
+int fold_stage_times(lfd_plan* p, int set) {
+  if (!p->ev_pending[set]) return LFD_OK;
+  float ms[4] = {0, 0, 0, 0};
+  LFD_CUDA(cudaEventSynchronize(p->ev[set][4]));
+  if (p->ev_has_project[set]) LFD_CUDA(cudaEventElapsedTime(&ms[0], p->ev[set][0], p->ev[set][1]));
+  LFD_CUDA(cudaEventElapsedTime(&ms[1], p->ev[set][1], p->ev[set][2]));
+  LFD_CUDA(cudaEventElapsedTime(&ms[2], p->ev[set][2], p->ev[set][3]));
+  LFD_CUDA(cudaEventElapsedTime(&ms[3], p->ev[set][3], p->ev[set][4]));
+  for (int a = 0; a < 4; ++a) p->acc_ms[a] += ms[a];
+  p->acc_frames += 1;
+  p->ev_pending[set] = false;
+  return LFD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lfd_version(void) { return 100; }
+
+const char* lfd_status_string(int status) {
+  switch (status) {
+    case LFD_OK:
+      return "ok";
+    case LFD_ERR_INVALID:
+      return "invalid argument";
+    case LFD_ERR_OOM:
+      return "out of device memory";
+    case LFD_ERR_CAPACITY:
+      return "pair count or key width beyond the supported limits";
+    case LFD_ERR_CUDA:
+      return "CUDA error";
+    case LFD_ERR_STATE:
+      return "requested data does not exist";
+    default:
+      return "unknown status";
+  }
+}
+
+const char* lfd_last_error(void) { return g_last_error; }
+
+void lfd_plan_destroy(lfd_plan* p) {
+  if (!p) return;
+  cudaSetDevice(p->device);
+  cudaDeviceSynchronize();
+  cudaFree(p->V);
+  cudaFree(p->psi);
+  cudaFree(p->n_sub);
+  cudaFree(p->seg);
+  DevBuf* bufs[] = {&p->proj_means, &p->proj_co,   &p->proj_ct,     &p->proj_depth,
+                    &p->item_key[0], &p->item_key[1], &p->item_val[0], &p->item_val[1],
+                    &p->counts,     &p->offsets,   &p->scan_tmp,    &p->pair_key[0],
+                    &p->pair_key[1], &p->pair_val[0], &p->pair_val[1], &p->radix_tmp,
+                    &p->ranges,     &p->small,     &p->host_in[0],  &p->host_in[1],
+                    &p->host_in[2], &p->host_in[3], &p->host_in[4], &p->image};
+  for (DevBuf* b : bufs) b->release();
+  if (p->h_small) cudaFreeHost(p->h_small);
+  for (auto& set : p->ev)
+    for (cudaEvent_t& e : set)
+      if (e) cudaEventDestroy(e);
+  delete p;
+}
+
+int lfd_plan_create(const lfd_panel* panel, const lfd_opts* opts, lfd_plan** out) {
+  if (!out) return fail(LFD_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!panel || !opts) return fail(LFD_ERR_INVALID, "panel or opts is NULL");
+  const lfd_panel& P = *panel;
+  const lfd_opts& O = *opts;
+  if (P.width <= 0 || P.height <= 0 || P.width > 65535 || P.height > 65535)
+    return fail(LFD_ERR_INVALID, "panel size out of range");
+  if (P.num_views < 1 || P.num_views > kMaxViews) return fail(LFD_ERR_INVALID, "num_views not in [1, 255]");
+  if (!(P.pitch > 0.0) || !isfinite(P.pitch) || !isfinite(P.tan_slant) || !isfinite(P.k_offset))
+    return fail(LFD_ERR_INVALID, "pitch must be > 0 and parameters finite");
+  if (O.tile_w < 4 || O.tile_h < 4 || O.tile_w > 64 || O.tile_h > 64 || O.tile_w * O.tile_h > 512)
+    return fail(LFD_ERR_INVALID, "tile shape out of range");
+  if (O.views_per_cluster < 1 || O.views_per_cluster > kMaxClusterViews)
+    return fail(LFD_ERR_INVALID, "views_per_cluster not in [1, 32]");
+  if (O.remap != 1) return fail(LFD_ERR_INVALID, "only the view-coherent remap (remap = 1) is built");
+  if (O.sort_mode != LFD_SORT_DEPTH_FIRST && O.sort_mode != LFD_SORT_KEY64)
+    return fail(LFD_ERR_INVALID, "unknown sort_mode");
+
+  lfd_plan* p = new (std::nothrow) lfd_plan();
+  if (!p) return fail(LFD_ERR_OOM, "host allocation failed");
+  p->panel = P;
+  p->opts = O;
+  cudaGetDevice(&p->device);
+  PanelGeom& g = p->g;
+  g.W = P.width;
+  g.H = P.height;
+  g.N = P.num_views;
+  g.C = O.views_per_cluster;
+  g.K = (g.N + g.C - 1) / g.C;
+  g.TW = O.tile_w;
+  g.TH = O.tile_h;
+  g.TX = (g.W + g.TW - 1) / g.TW;
+  g.TY = (g.H + g.TH - 1) / g.TH;
+  g.T = g.TX * g.TY;
+  g.cap = 3 * g.TW * g.TH;
+  g.bit_k = ceil_log2((uint64_t)g.K);
+  g.bit_t = ceil_log2((uint64_t)g.T);
+  if (g.bit_t + g.bit_k > 32) {
+    delete p;
+    return fail(LFD_ERR_CAPACITY, "tile and cluster bits exceed 32");
+  }
+  int rc = LFD_OK;
+  auto cleanup = [&](int code) {
+    lfd_plan_destroy(p);
+    return code;
+  };
+  const size_t nsub = (size_t)g.W * g.H * 3;
+  cudaError_t e;
+  if ((e = cudaMalloc(&p->V, nsub)) != cudaSuccess) return cleanup(fail_cuda(e, "cudaMalloc V"));
+  if ((e = cudaMalloc(&p->psi, (size_t)g.T * g.cap * sizeof(uint32_t))) != cudaSuccess)
+    return cleanup(fail_cuda(e, "cudaMalloc psi"));
+  if ((e = cudaMalloc(&p->n_sub, (size_t)g.T * sizeof(int32_t))) != cudaSuccess)
+    return cleanup(fail_cuda(e, "cudaMalloc n_sub"));
+  if ((e = cudaMalloc(&p->seg, (size_t)g.T * (g.K + 1) * sizeof(int32_t))) != cudaSuccess)
+    return cleanup(fail_cuda(e, "cudaMalloc seg"));
+  if ((e = cudaMallocHost(&p->h_small, 4 * sizeof(unsigned long long))) != cudaSuccess)
+    return cleanup(fail_cuda(e, "cudaMallocHost"));
+  if ((rc = p->small.ensure(4 * sizeof(unsigned long long))) != LFD_OK) return cleanup(rc);
+  for (auto& set : p->ev)
+    for (cudaEvent_t& ev : set)
+      if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cleanup(fail_cuda(e, "cudaEventCreate"));
+  if ((e = launch_view_index(g.W, g.H, g.N, P.tan_slant, P.pitch, P.k_offset, p->V, 0)) != cudaSuccess)
+    return cleanup(fail_cuda(e, "view_index"));
+  if ((e = launch_remap(g, p->V, p->psi, p->n_sub, p->seg, 0)) != cudaSuccess)
+    return cleanup(fail_cuda(e, "remap"));
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cleanup(fail_cuda(e, "plan build"));
+  // longest (tile, cluster) run, for the blend launch shape
+  int32_t* hseg = (int32_t*)malloc((size_t)g.T * (g.K + 1) * sizeof(int32_t));
+  if (!hseg) return cleanup(fail(LFD_ERR_OOM, "host allocation failed"));
+  e = cudaMemcpy(hseg, p->seg, (size_t)g.T * (g.K + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    free(hseg);
+    return cleanup(fail_cuda(e, "copy seg"));
+  }
+  int mx = 0;
+  for (int t = 0; t < g.T; ++t)
+    for (int k = 0; k < g.K; ++k) {
+      const int n = hseg[(size_t)t * (g.K + 1) + k + 1] - hseg[(size_t)t * (g.K + 1) + k];
+      mx = n > mx ? n : mx;
+    }
+  free(hseg);
+  p->max_segment = mx;
+  *out = p;
+  return LFD_OK;
+}
+
+int lfd_plan_get_info(const lfd_plan* p, lfd_plan_info* out) {
+  if (!p || !out) return fail(LFD_ERR_INVALID, "NULL argument");
+  out->num_clusters = p->g.K;
+  out->tiles_x = p->g.TX;
+  out->tiles_y = p->g.TY;
+  out->tile_capacity = p->g.cap;
+  out->bit_k = p->g.bit_k;
+  out->bit_t = p->g.bit_t;
+  out->max_segment = p->max_segment;
+  return LFD_OK;
+}
+
+int lfd_set_flags(lfd_plan* p, int32_t flags) {
+  if (!p) return fail(LFD_ERR_INVALID, "NULL plan");
+  if (flags & ~(LFD_FLAG_STAGE_TIMING | LFD_FLAG_COUNT_EVALS)) return fail(LFD_ERR_INVALID, "unknown flag");
+  p->flags = flags;
+  return LFD_OK;
+}
+
+int lfd_plan_copy_tables(const lfd_plan* p, uint8_t* V, uint16_t* psi, int32_t* n_sub, int32_t* seg) {
+  if (!p) return fail(LFD_ERR_INVALID, "NULL plan");
+  const PanelGeom& g = p->g;
+  if (V) LFD_CUDA(cudaMemcpy(V, p->V, (size_t)g.W * g.H * 3, cudaMemcpyDeviceToHost));
+  if (psi) {
+    const size_t n = (size_t)g.T * g.cap;
+    uint32_t* tmp = (uint32_t*)malloc(n * sizeof(uint32_t));
+    if (!tmp) return fail(LFD_ERR_OOM, "host allocation failed");
+    cudaError_t e = cudaMemcpy(tmp, p->psi, n * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      free(tmp);
+      return fail_cuda(e, "copy psi");
+    }
+    for (size_t a = 0; a < n; ++a) psi[a] = (uint16_t)(tmp[a] & 0xffffu);
+    free(tmp);
+  }
+  if (n_sub) LFD_CUDA(cudaMemcpy(n_sub, p->n_sub, (size_t)g.T * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (seg)
+    LFD_CUDA(cudaMemcpy(seg, p->seg, (size_t)g.T * (g.K + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  return LFD_OK;
+}
+
+static int check_gaussians(const lfd_plan* p, const lfd_gaussians* gs) {
+  if (!gs) return fail(LFD_ERR_INVALID, "gaussians is NULL");
+  if (gs->count < 0) return fail(LFD_ERR_INVALID, "negative Gaussian count");
+  if (gs->sh_degree < 0 || gs->sh_degree > 3) return fail(LFD_ERR_INVALID, "sh_degree not in [0, 3]");
+  if ((uint64_t)gs->count * (uint64_t)p->g.K >= (1ull << 32))
+    return fail(LFD_ERR_CAPACITY, "count * clusters must stay below 2^32");
+  if (gs->count > 0) {
+    if (!gs->means || !gs->scales || !gs->quats || !gs->opacities || !gs->sh)
+      return fail(LFD_ERR_INVALID, "NULL Gaussian attribute");
+    if (!aligned(gs->quats, 16)) return fail(LFD_ERR_INVALID, "quats must be 16-byte aligned");
+  }
+  return LFD_OK;
+}
+
+static int fill_cams(const lfd_plan* p, const lfd_camera* cams, int32_t num_cams, CamTable* t) {
+  if (!cams) return fail(LFD_ERR_INVALID, "cams is NULL");
+  if (num_cams != p->g.N) return fail(LFD_ERR_INVALID, "num_cams must equal the panel's num_views");
+  memset(t, 0, sizeof(*t));
+  for (int j = 0; j < num_cams; ++j) {
+    memcpy(t->c[j], cams[j].R, 9 * sizeof(float));
+    memcpy(t->c[j] + 9, cams[j].t, 3 * sizeof(float));
+    t->c[j][12] = cams[j].fx;
+    t->c[j][13] = cams[j].fy;
+    t->c[j][14] = cams[j].cx;
+    t->c[j][15] = cams[j].cy;
+  }
+  return LFD_OK;
+}
+
+int lfd_project(lfd_plan* p, const lfd_gaussians* gs, const lfd_camera* cams, int32_t num_cams,
+                float* means2d, float* conic_opacity, float* color_tau, float* depth, void* stream) {
+  if (!p) return fail(LFD_ERR_INVALID, "NULL plan");
+  int rc = check_gaussians(p, gs);
+  if (rc != LFD_OK) return rc;
+  CamTable* t = new (std::nothrow) CamTable;
+  if (!t) return fail(LFD_ERR_OOM, "host allocation failed");
+  rc = fill_cams(p, cams, num_cams, t);
+  if (rc == LFD_OK && gs->count > 0) {
+    if (!means2d || !conic_opacity || !color_tau || !depth)
+      rc = fail(LFD_ERR_INVALID, "NULL output buffer");
+    else if (!aligned(conic_opacity, 16) || !aligned(color_tau, 16) || !aligned(means2d, 8))
+      rc = fail(LFD_ERR_INVALID, "output buffers misaligned");
+  }
+  if (rc == LFD_OK) {
+    ProjectArgs a;
+    a.means = gs->means;
+    a.scales = gs->scales;
+    a.quats = gs->quats;
+    a.opac = gs->opacities;
+    a.sh = gs->sh;
+    a.M = gs->count;
+    a.sh_degree = gs->sh_degree;
+    a.means2d = means2d;
+    a.conic_opacity = conic_opacity;
+    a.color_tau = color_tau;
+    a.depth = depth;
+    cudaError_t e = launch_project(p->g, *t, a, (cudaStream_t)stream);
+    if (e != cudaSuccess) rc = fail_cuda(e, "project");
+  }
+  delete t;
+  return rc;
+}
+
+static int render_projected_impl(lfd_plan* p, int64_t M, const float* means2d,
+                                 const float* conic_opacity, const float* color_tau,
+                                 const float* depth, float* out_rgb, void* stream, lfd_stats* stats,
+                                 bool projected_here) {
+  if (!p) return fail(LFD_ERR_INVALID, "NULL plan");
+  const PanelGeom& g = p->g;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (M < 0) return fail(LFD_ERR_INVALID, "negative Gaussian count");
+  if ((uint64_t)M * (uint64_t)g.K >= (1ull << 32)) return fail(LFD_ERR_CAPACITY, "M * K must stay below 2^32");
+  if (!out_rgb) return fail(LFD_ERR_INVALID, "out_rgb is NULL");
+  if (M > 0 && (!means2d || !conic_opacity || !color_tau || !depth))
+    return fail(LFD_ERR_INVALID, "NULL attribute buffer");
+  if (M > 0 && (!aligned(conic_opacity, 16) || !aligned(color_tau, 16) || !aligned(means2d, 8)))
+    return fail(LFD_ERR_INVALID, "attribute buffers misaligned");
+  const bool timing = (p->flags & LFD_FLAG_STAGE_TIMING) != 0;
+  const bool counting = (p->flags & LFD_FLAG_COUNT_EVALS) != 0;
+  const bool key64 = p->opts.sort_mode == LFD_SORT_KEY64;
+  const int64_t n_items = (int64_t)g.K * M;
+  int rc;
+  unsigned long long* d_small = p->small.as<unsigned long long>();
+  const int es = p->ev_set;
+  cudaEvent_t* ev = p->ev[es];
+  if (timing) {
+    if (!projected_here) LFD_CUDA(cudaEventRecord(ev[0], s));
+    LFD_CUDA(cudaEventRecord(ev[1], s));
+  }
+
+  // ---- stage 2: key generation ----
+  if ((rc = p->counts.ensure((size_t)(n_items + 1) * 4)) != LFD_OK) return rc;
+  if ((rc = p->offsets.ensure((size_t)(n_items + 1) * 4)) != LFD_OK) return rc;
+  if ((rc = p->scan_tmp.ensure(scan_temp_bytes(n_items + 1))) != LFD_OK) return rc;
+  const uint32_t* order = nullptr;
+  if (!key64) {
+    // depth-first order: sort the K*M (cluster, depth) items once
+    for (int b = 0; b < 2; ++b) {
+      if ((rc = p->item_key[b].ensure((size_t)(n_items + 1) * 8)) != LFD_OK) return rc;
+      if ((rc = p->item_val[b].ensure((size_t)(n_items + 1) * 4)) != LFD_OK) return rc;
+    }
+    if ((rc = p->radix_tmp.ensure(radix_temp_bytes(n_items))) != LFD_OK) return rc;
+    LFD_CUDA(launch_item_keys(g, M, depth, color_tau, p->item_key[0].as<uint64_t>(),
+                              p->item_val[0].as<uint32_t>(), s));
+    bool alt = false;
+    LFD_CUDA(radix_sort_u64(p->item_key[0].as<uint64_t>(), p->item_key[1].as<uint64_t>(),
+                            p->item_val[0].as<uint32_t>(), p->item_val[1].as<uint32_t>(), n_items,
+                            32 + g.bit_k, p->radix_tmp.p, &alt, s));
+    order = p->item_val[alt ? 1 : 0].as<uint32_t>();
+  }
+  LFD_CUDA(launch_bin_count(g, M, means2d, conic_opacity, color_tau, order, n_items,
+                            p->counts.as<uint32_t>(), s));
+  LFD_CUDA(scan_exclusive(p->counts.as<uint32_t>(), p->offsets.as<uint32_t>(), n_items, p->scan_tmp.p,
+                          d_small, s));
+  LFD_CUDA(cudaMemcpyAsync(p->h_small, d_small, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  LFD_CUDA(cudaStreamSynchronize(s));
+  if ((rc = fold_stage_times(p, es ^ 1)) != LFD_OK) return rc;
+  const unsigned long long P = p->h_small[0];
+  if (P >= 0xffffffffull) return fail(LFD_ERR_CAPACITY, "more than 2^32 - 1 Gaussian-tile pairs");
+  const size_t kbytes = key64 ? 8 : 4;
+  for (int b = 0; b < 2; ++b) {
+    if ((rc = p->pair_key[b].ensure((size_t)(P + 1) * kbytes)) != LFD_OK) return rc;
+    if ((rc = p->pair_val[b].ensure((size_t)(P + 1) * 4)) != LFD_OK) return rc;
+  }
+  if ((rc = p->radix_tmp.ensure(radix_temp_bytes((int64_t)P))) != LFD_OK) return rc;
+  if ((rc = p->ranges.ensure((size_t)g.T * g.K * sizeof(uint2))) != LFD_OK) return rc;
+  LFD_CUDA(launch_bin_emit(g, M, means2d, conic_opacity, color_tau, depth, order, n_items,
+                           p->offsets.as<uint32_t>(), key64 ? nullptr : p->pair_key[0].as<uint32_t>(),
+                           key64 ? p->pair_key[0].as<uint64_t>() : nullptr,
+                           p->pair_val[0].as<uint32_t>(), s));
+  if (timing) LFD_CUDA(cudaEventRecord(ev[2], s));
+
+  // ---- stage 3: sort by (tile, cluster[, depth]) ----
+  bool alt = false;
+  if (key64)
+    LFD_CUDA(radix_sort_u64(p->pair_key[0].as<uint64_t>(), p->pair_key[1].as<uint64_t>(),
+                            p->pair_val[0].as<uint32_t>(), p->pair_val[1].as<uint32_t>(), (int64_t)P,
+                            32 + g.bit_k + g.bit_t, p->radix_tmp.p, &alt, s));
+  else
+    LFD_CUDA(radix_sort_u32(p->pair_key[0].as<uint32_t>(), p->pair_key[1].as<uint32_t>(),
+                            p->pair_val[0].as<uint32_t>(), p->pair_val[1].as<uint32_t>(), (int64_t)P,
+                            g.bit_k + g.bit_t, p->radix_tmp.p, &alt, s));
+  const int kb = alt ? 1 : 0;
+  LFD_CUDA(cudaMemsetAsync(p->ranges.p, 0, (size_t)g.T * g.K * sizeof(uint2), s));
+  LFD_CUDA(launch_ranges(g, (int64_t)P, key64 ? nullptr : p->pair_key[kb].as<uint32_t>(),
+                         key64 ? p->pair_key[kb].as<uint64_t>() : nullptr, p->ranges.as<uint2>(), s));
+  if (timing) LFD_CUDA(cudaEventRecord(ev[3], s));
+
+  // ---- stage 4: subpixel blend with view-coherent remapping ----
+  if (counting) LFD_CUDA(cudaMemsetAsync(d_small + 1, 0, sizeof(unsigned long long), s));
+  BlendArgs ba;
+  ba.psi = p->psi;
+  ba.seg = p->seg;
+  ba.ranges = p->ranges.as<uint2>();
+  ba.list = p->pair_val[kb].as<uint32_t>();
+  ba.means2d = means2d;
+  ba.conic_opacity = conic_opacity;
+  ba.color_tau = color_tau;
+  ba.M = M;
+  ba.bg[0] = p->opts.bg[0];
+  ba.bg[1] = p->opts.bg[1];
+  ba.bg[2] = p->opts.bg[2];
+  ba.out = out_rgb;
+  ba.eval_counter = counting ? d_small + 1 : nullptr;
+  ba.max_segment = p->max_segment;
+  LFD_CUDA(launch_blend(g, ba, s));
+  if (timing) {
+    LFD_CUDA(cudaEventRecord(ev[4], s));
+    p->ev_pending[es] = true;
+    p->ev_has_project[es] = projected_here;
+    p->ev_set = es ^ 1;
+  }
+
+  p->last_P = (int64_t)P;
+  p->last_key_buf = kb;
+  p->last_val_buf = kb;
+  p->last_sort_mode = p->opts.sort_mode;
+  p->last_stream = s;
+  if (stats) {
+    stats->num_pairs = (int64_t)P;
+    stats->num_evals = -1;
+    stats->ms_project = stats->ms_keygen = stats->ms_sort = stats->ms_blend = -1.f;
+    if (counting || timing) {
+      if (counting)
+        LFD_CUDA(cudaMemcpyAsync(p->h_small + 1, d_small + 1, sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, s));
+      LFD_CUDA(cudaStreamSynchronize(s));
+      if (counting) stats->num_evals = (int64_t)p->h_small[1];
+      if (timing) {
+        if (projected_here) LFD_CUDA(cudaEventElapsedTime(&stats->ms_project, ev[0], ev[1]));
+        LFD_CUDA(cudaEventElapsedTime(&stats->ms_keygen, ev[1], ev[2]));
+        LFD_CUDA(cudaEventElapsedTime(&stats->ms_sort, ev[2], ev[3]));
+        LFD_CUDA(cudaEventElapsedTime(&stats->ms_blend, ev[3], ev[4]));
+      }
+    }
+  }
+  return LFD_OK;
+}
+
+int lfd_render_projected(lfd_plan* p, int64_t M, const float* means2d, const float* conic_opacity,
+                         const float* color_tau, const float* depth, float* out_rgb, void* stream,
+                         lfd_stats* stats) {
+  return render_projected_impl(p, M, means2d, conic_opacity, color_tau, depth, out_rgb, stream,
+                               stats, false);
+}
+
+int lfd_render(lfd_plan* p, const lfd_gaussians* gs, const lfd_camera* cams, int32_t num_cams,
+               float* out_rgb, void* stream, lfd_stats* stats) {
+  if (!p) return fail(LFD_ERR_INVALID, "NULL plan");
+  int rc = check_gaussians(p, gs);
+  if (rc != LFD_OK) return rc;
+  const PanelGeom& g = p->g;
+  const int64_t M = gs->count;
+  const int64_t n_items = (int64_t)g.K * M;
+  if ((rc = p->proj_means.ensure((size_t)(n_items * g.C + 1) * 8)) != LFD_OK) return rc;
+  if ((rc = p->proj_co.ensure((size_t)(n_items + 1) * 16)) != LFD_OK) return rc;
+  if ((rc = p->proj_ct.ensure((size_t)(n_items + 1) * 16)) != LFD_OK) return rc;
+  if ((rc = p->proj_depth.ensure((size_t)(n_items + 1) * 4)) != LFD_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool timing = (p->flags & LFD_FLAG_STAGE_TIMING) != 0;
+  if (timing) LFD_CUDA(cudaEventRecord(p->ev[p->ev_set][0], s));
+  rc = lfd_project(p, gs, cams, num_cams, p->proj_means.as<float>(), p->proj_co.as<float>(),
+                   p->proj_ct.as<float>(), p->proj_depth.as<float>(), stream);
+  if (rc != LFD_OK) return rc;
+  return render_projected_impl(p, M, p->proj_means.as<float>(), p->proj_co.as<float>(),
+                               p->proj_ct.as<float>(), p->proj_depth.as<float>(), out_rgb, stream,
+                               stats, true);
+}
+
+int lfd_render_host(lfd_plan* p, const lfd_gaussians* gh, const lfd_camera* cams, int32_t num_cams,
+                    float* out_rgb_host, void* stream, lfd_stats* stats) {
+  if (!p) return fail(LFD_ERR_INVALID, "NULL plan");
+  if (!out_rgb_host) return fail(LFD_ERR_INVALID, "out_rgb_host is NULL");
+  if (!gh) return fail(LFD_ERR_INVALID, "gaussians is NULL");
+  const int64_t M = gh->count;
+  if (M < 0 || gh->sh_degree < 0 || gh->sh_degree > 3) return fail(LFD_ERR_INVALID, "bad Gaussian set");
+  const int ncoef = (gh->sh_degree + 1) * (gh->sh_degree + 1);
+  const size_t bytes[5] = {(size_t)M * 12, (size_t)M * 12, (size_t)M * 16, (size_t)M * 4,
+                           (size_t)M * ncoef * 12};
+  const void* src[5] = {gh->means, gh->scales, gh->quats, gh->opacities, gh->sh};
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc;
+  for (int b = 0; b < 5; ++b) {
+    if ((rc = p->host_in[b].ensure(bytes[b] + 16)) != LFD_OK) return rc;
+    if (M > 0) {
+      if (!src[b]) return fail(LFD_ERR_INVALID, "NULL Gaussian attribute");
+      LFD_CUDA(cudaMemcpyAsync(p->host_in[b].p, src[b], bytes[b], cudaMemcpyHostToDevice, s));
+    }
+  }
+  const size_t out_bytes = (size_t)p->g.W * p->g.H * 3 * sizeof(float);
+  if ((rc = p->image.ensure(out_bytes)) != LFD_OK) return rc;
+  lfd_gaussians gd = *gh;
+  gd.means = p->host_in[0].as<float>();
+  gd.scales = p->host_in[1].as<float>();
+  gd.quats = p->host_in[2].as<float>();
+  gd.opacities = p->host_in[3].as<float>();
+  gd.sh = p->host_in[4].as<float>();
+  rc = lfd_render(p, &gd, cams, num_cams, p->image.as<float>(), stream, stats);
+  if (rc != LFD_OK) return rc;
+  LFD_CUDA(cudaMemcpyAsync(out_rgb_host, p->image.p, out_bytes, cudaMemcpyDeviceToHost, s));
+  LFD_CUDA(cudaStreamSynchronize(s));
+  return LFD_OK;
+}
+
+int lfd_plan_copy_lists(const lfd_plan* p, uint32_t* list, uint32_t* ranges, uint64_t* keys,
+                        int64_t capacity) {
+  if (!p) return fail(LFD_ERR_INVALID, "NULL plan");
+  if (p->last_P < 0) return fail(LFD_ERR_STATE, "no frame rendered yet");
+  if (keys && p->last_sort_mode != LFD_SORT_KEY64)
+    return fail(LFD_ERR_STATE, "keys exist only with LFD_SORT_KEY64");
+  LFD_CUDA(cudaStreamSynchronize(p->last_stream));
+  const int64_t P = p->last_P;
+  if ((list || keys) && capacity < P) return fail(LFD_ERR_INVALID, "capacity below the pair count");
+  if (list && P > 0)
+    LFD_CUDA(cudaMemcpy(list, p->pair_val[p->last_val_buf].p, (size_t)P * 4, cudaMemcpyDeviceToHost));
+  if (keys && P > 0)
+    LFD_CUDA(cudaMemcpy(keys, p->pair_key[p->last_key_buf].p, (size_t)P * 8, cudaMemcpyDeviceToHost));
+  if (ranges)
+    LFD_CUDA(cudaMemcpy(ranges, p->ranges.p, (size_t)p->g.T * p->g.K * sizeof(uint2),
+                        cudaMemcpyDeviceToHost));
+  return LFD_OK;
+}
+
+int lfd_get_stage_totals(lfd_plan* p, lfd_stage_times* out, int32_t reset) {
+  if (!p || !out) return fail(LFD_ERR_INVALID, "NULL argument");
+  if (p->ev_pending[0] || p->ev_pending[1]) {
+    LFD_CUDA(cudaStreamSynchronize(p->last_stream));
+    int rc;
+    // fold the older set first so frames are counted in order
+    const int older = p->ev_set;
+    if ((rc = fold_stage_times(p, older)) != LFD_OK) return rc;
+    if ((rc = fold_stage_times(p, older ^ 1)) != LFD_OK) return rc;
+  }
+  out->frames = p->acc_frames;
+  out->ms_project = p->acc_ms[0];
+  out->ms_keygen = p->acc_ms[1];
+  out->ms_sort = p->acc_ms[2];
+  out->ms_blend = p->acc_ms[3];
+  if (reset) {
+    p->acc_frames = 0;
+    for (double& a : p->acc_ms) a = 0.0;
+  }
+  return LFD_OK;
+}
+
+uint64_t lfd_kernel_launches(void) { return lfd::launch_count(); }
+
+}  // extern "C"

@@ -1,0 +1,102 @@
+// Internal declarations shared by the CUDA translation units of liblfd.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lfd.h"
+
+namespace lfd {
+
+constexpr int kMaxViews = 255;
+constexpr int kMaxClusterViews = 32;
+constexpr int kMaxTileSubpixels = 3 * 512;
+
+// Per-launch camera table: passed by value as a kernel parameter (large
+// kernel parameters, 16 KB here), so concurrent frames never share state.
+struct CamTable {
+  float c[kMaxViews][16];  // R[9], t[3], fx, fy, cx, cy
+};
+
+// Every kernel launch of the library is counted (lfd_kernel_launches()).
+void note_launches(int n);
+uint64_t launch_count();
+
+struct PanelGeom {
+  int W, H, N, C, K;
+  int TW, TH, TX, TY, T;
+  int cap;  // 3 * TW * TH
+  int bit_k, bit_t;
+};
+
+// ---- plan tables (plan_kernels.cu) ----
+cudaError_t launch_view_index(int W, int H, int N, double tan_slant, double pitch,
+                              double k_offset, uint8_t* V, cudaStream_t s);
+cudaError_t launch_remap(const PanelGeom& g, const uint8_t* V, uint32_t* psi,
+                         int32_t* n_sub, int32_t* seg, cudaStream_t s);
+
+// ---- projection (project.cu) ----
+struct ProjectArgs {
+  const float *means, *scales, *quats, *opac, *sh;
+  int64_t M;
+  int sh_degree;
+  float* means2d;        // [K][M][C][2]
+  float* conic_opacity;  // [K][M][4]
+  float* color_tau;      // [K][M][4]
+  float* depth;          // [K][M]
+};
+cudaError_t launch_project(const PanelGeom& g, const CamTable& cams, const ProjectArgs& a,
+                           cudaStream_t s);
+
+// ---- key generation (binning.cu) ----
+// item keys for the depth-first order: (k << 32) | depth bits, value k*M + i
+cudaError_t launch_item_keys(const PanelGeom& g, int64_t M, const float* depth,
+                             const float* color_tau, uint64_t* keys, uint32_t* vals,
+                             cudaStream_t s);
+// tile count of the cluster union per item; items given by `order` (flat
+// k*M + i indices) or natural order when order == nullptr
+cudaError_t launch_bin_count(const PanelGeom& g, int64_t M, const float* means2d,
+                             const float* conic_opacity, const float* color_tau,
+                             const uint32_t* order, int64_t n_items, uint32_t* counts,
+                             cudaStream_t s);
+// emission: key32 = (t << bit_k) | k when keys64 == nullptr, else Eq. 11
+cudaError_t launch_bin_emit(const PanelGeom& g, int64_t M, const float* means2d,
+                            const float* conic_opacity, const float* color_tau,
+                            const float* depth, const uint32_t* order, int64_t n_items,
+                            const uint32_t* offsets, uint32_t* keys32, uint64_t* keys64,
+                            uint32_t* vals, cudaStream_t s);
+cudaError_t launch_ranges(const PanelGeom& g, int64_t P, const uint32_t* keys32,
+                          const uint64_t* keys64, uint2* ranges, cudaStream_t s);
+
+// ---- scan and radix sort (sort.cu) ----
+size_t scan_temp_bytes(int64_t n);
+// exclusive scan of n uint32 into out; the 64-bit total goes to *total_dev
+cudaError_t scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, void* temp,
+                           unsigned long long* total_dev, cudaStream_t s);
+size_t radix_temp_bytes(int64_t n);
+// stable LSD radix sort of (key, value) over bits [0, bits); ping-pongs
+// between the two buffers; *result_in_alt tells where the result ends up
+cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals,
+                           uint32_t* vals_alt, int64_t n, int bits, void* temp,
+                           bool* result_in_alt, cudaStream_t s);
+cudaError_t radix_sort_u64(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals,
+                           uint32_t* vals_alt, int64_t n, int bits, void* temp,
+                           bool* result_in_alt, cudaStream_t s);
+
+// ---- blend (blend.cu) ----
+struct BlendArgs {
+  const uint32_t* psi;  // [T][cap] packed (view << 16) | local index
+  const int32_t* seg;   // [T][K+1]
+  const uint2* ranges;  // [T][K]
+  const uint32_t* list;
+  const float* means2d;
+  const float* conic_opacity;
+  const float* color_tau;
+  int64_t M;
+  float bg[3];
+  float* out;
+  unsigned long long* eval_counter;  // non-null: count visited entries
+  int max_segment;
+};
+cudaError_t launch_blend(const PanelGeom& g, const BlendArgs& a, cudaStream_t s);
+
+}  // namespace lfd

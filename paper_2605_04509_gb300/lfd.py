@@ -1,0 +1,294 @@
+"""Thin ctypes binding of liblfd.so (include/lfd.h).
+
+Argument marshalling only: every step of the renderer runs in the library's
+CUDA kernels. PyTorch supplies device memory and streams. If the library has
+not been built, every entry point raises; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+from typing import Dict, Optional, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblfd.so")
+
+LFD_OK = 0
+LFD_ERR_INVALID = -1
+LFD_ERR_OOM = -2
+LFD_ERR_CAPACITY = -3
+LFD_ERR_CUDA = -4
+LFD_ERR_STATE = -5
+SORT_DEPTH_FIRST = 0
+SORT_KEY64 = 1
+FLAG_STAGE_TIMING = 1
+FLAG_COUNT_EVALS = 2
+
+
+class LFDError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"lfd status {status}: {message}")
+        self.status = status
+
+
+class CPanel(ct.Structure):
+    _fields_ = [("width", ct.c_int32), ("height", ct.c_int32), ("num_views", ct.c_int32),
+                ("tan_slant", ct.c_double), ("pitch", ct.c_double), ("k_offset", ct.c_double)]
+
+
+class COpts(ct.Structure):
+    _fields_ = [("tile_w", ct.c_int32), ("tile_h", ct.c_int32),
+                ("views_per_cluster", ct.c_int32), ("remap", ct.c_int32),
+                ("sort_mode", ct.c_int32), ("bg", ct.c_float * 3)]
+
+
+class CGaussians(ct.Structure):
+    _fields_ = [("means", ct.c_void_p), ("scales", ct.c_void_p), ("quats", ct.c_void_p),
+                ("opacities", ct.c_void_p), ("sh", ct.c_void_p), ("count", ct.c_int64),
+                ("sh_degree", ct.c_int32)]
+
+
+class CCamera(ct.Structure):
+    _fields_ = [("v", ct.c_float * 16)]
+
+
+class CPlanInfo(ct.Structure):
+    _fields_ = [("num_clusters", ct.c_int32), ("tiles_x", ct.c_int32), ("tiles_y", ct.c_int32),
+                ("tile_capacity", ct.c_int32), ("bit_k", ct.c_int32), ("bit_t", ct.c_int32),
+                ("max_segment", ct.c_int32)]
+
+
+class CStats(ct.Structure):
+    _fields_ = [("num_pairs", ct.c_int64), ("num_evals", ct.c_int64),
+                ("ms_project", ct.c_float), ("ms_keygen", ct.c_float),
+                ("ms_sort", ct.c_float), ("ms_blend", ct.c_float)]
+
+    def as_dict(self) -> Dict[str, float]:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class CStageTotals(ct.Structure):
+    _fields_ = [("frames", ct.c_int64), ("ms_project", ct.c_double), ("ms_keygen", ct.c_double),
+                ("ms_sort", ct.c_double), ("ms_blend", ct.c_double)]
+
+
+_lib = None
+_P = ct.c_void_p
+
+
+def load() -> ct.CDLL:
+    """Load liblfd.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise LFDError(LFD_ERR_STATE, f"{LIB_PATH} is missing: build it with "
+                           "paper_2605_04509_gb300.build_lib.build()")
+        L = ct.CDLL(LIB_PATH)
+        sig = {
+            "lfd_plan_create": ([ct.POINTER(CPanel), ct.POINTER(COpts), ct.POINTER(_P)], ct.c_int),
+            "lfd_plan_destroy": ([_P], None),
+            "lfd_plan_get_info": ([_P, ct.POINTER(CPlanInfo)], ct.c_int),
+            "lfd_set_flags": ([_P, ct.c_int32], ct.c_int),
+            "lfd_plan_copy_tables": ([_P, _P, _P, _P, _P], ct.c_int),
+            "lfd_project": ([_P, ct.POINTER(CGaussians), ct.POINTER(CCamera), ct.c_int32,
+                             _P, _P, _P, _P, _P], ct.c_int),
+            "lfd_render_projected": ([_P, ct.c_int64, _P, _P, _P, _P, _P, _P,
+                                      ct.POINTER(CStats)], ct.c_int),
+            "lfd_render": ([_P, ct.POINTER(CGaussians), ct.POINTER(CCamera), ct.c_int32, _P, _P,
+                            ct.POINTER(CStats)], ct.c_int),
+            "lfd_render_host": ([_P, ct.POINTER(CGaussians), ct.POINTER(CCamera), ct.c_int32,
+                                 _P, _P, ct.POINTER(CStats)], ct.c_int),
+            "lfd_plan_copy_lists": ([_P, _P, _P, _P, ct.c_int64], ct.c_int),
+            "lfd_get_stage_totals": ([_P, ct.POINTER(CStageTotals), ct.c_int32], ct.c_int),
+            "lfd_kernel_launches": ([], ct.c_uint64),
+            "lfd_status_string": ([ct.c_int], ct.c_char_p),
+            "lfd_last_error": ([], ct.c_char_p),
+            "lfd_version": ([], ct.c_int),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != LFD_OK:
+        L = load()
+        raise LFDError(rc, f"{L.lfd_status_string(rc).decode()}: {L.lfd_last_error().decode()}")
+
+
+def _dptr(t) -> int:
+    """Device pointer of a torch CUDA tensor (or 0 for None)."""
+    if t is None:
+        return 0
+    assert t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    return t.data_ptr()
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def cameras_array(cams: np.ndarray):
+    cams = np.ascontiguousarray(cams, dtype=np.float32).reshape(-1, 16)
+    arr = (CCamera * len(cams))()
+    ct.memmove(arr, cams.ctypes.data, cams.nbytes)
+    return arr, len(cams)
+
+
+def num_sh_degree(sh_shape) -> int:
+    ncoef = sh_shape[1]
+    return {1: 0, 4: 1, 9: 2, 16: 3}[ncoef]
+
+
+def gaussians_struct(scene, host: bool = False) -> CGaussians:
+    """scene: dict of contiguous float32 tensors means [M,3], scales [M,3],
+    quats [M,4], opacities [M], sh [M,(d+1)^2,3] (CUDA, or CPU for host=True)."""
+    g = CGaussians()
+    ptr = (lambda t: t.data_ptr()) if host else _dptr
+    g.means = ptr(scene["means"])
+    g.scales = ptr(scene["scales"])
+    g.quats = ptr(scene["quats"])
+    g.opacities = ptr(scene["opacities"])
+    g.sh = ptr(scene["sh"])
+    g.count = int(scene["means"].shape[0])
+    g.sh_degree = num_sh_degree(tuple(scene["sh"].shape))
+    return g
+
+
+class Plan:
+    """A panel + options plan (lfd_plan_create); owns V, Psi and scratch."""
+
+    def __init__(self, panel, tile: Tuple[int, int] = (16, 16), views_per_cluster: int = 8,
+                 sort_mode: int = SORT_DEPTH_FIRST, bg=(0.0, 0.0, 0.0)):
+        L = load()
+        self.panel = panel
+        cp = CPanel(panel.width, panel.height, panel.num_views, float(panel.tan_slant),
+                    float(panel.pitch), float(panel.k_offset))
+        co = COpts(tile[0], tile[1], views_per_cluster, 1, sort_mode, (ct.c_float * 3)(*bg))
+        h = _P()
+        _check(L.lfd_plan_create(ct.byref(cp), ct.byref(co), ct.byref(h)))
+        self._h = h
+        self.tile = tuple(tile)
+        self.views_per_cluster = views_per_cluster
+        self.sort_mode = sort_mode
+        info = CPlanInfo()
+        _check(L.lfd_plan_get_info(h, ct.byref(info)))
+        self.info = {f: getattr(info, f) for f, _ in info._fields_}
+        self.K = self.info["num_clusters"]
+        self.T = self.info["tiles_x"] * self.info["tiles_y"]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().lfd_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_flags(self, flags: int):
+        _check(load().lfd_set_flags(self._h, flags))
+
+    def tables(self):
+        p = self.panel
+        V = np.zeros((p.height, p.width, 3), np.uint8)
+        cap = self.info["tile_capacity"]
+        psi = np.zeros((self.T, cap), np.uint16)
+        n_sub = np.zeros(self.T, np.int32)
+        seg = np.zeros((self.T, self.K + 1), np.int32)
+        _check(load().lfd_plan_copy_tables(self._h, V.ctypes.data, psi.ctypes.data,
+                                           n_sub.ctypes.data, seg.ctypes.data))
+        return V, psi, n_sub, seg
+
+    def alloc_projected(self, M: int):
+        import torch
+        C, K = self.views_per_cluster, self.K
+        dev = torch.device("cuda")
+        return {
+            "means2d": torch.empty((K, M, C, 2), dtype=torch.float32, device=dev),
+            "conic_opacity": torch.empty((K, M, 4), dtype=torch.float32, device=dev),
+            "color_tau": torch.empty((K, M, 4), dtype=torch.float32, device=dev),
+            "depth": torch.empty((K, M), dtype=torch.float32, device=dev),
+        }
+
+    def project(self, scene, cams: np.ndarray, out=None, stream=None):
+        M = int(scene["means"].shape[0])
+        out = out if out is not None else self.alloc_projected(M)
+        g = gaussians_struct(scene)
+        carr, n = cameras_array(cams)
+        _check(load().lfd_project(self._h, ct.byref(g), carr, n, _dptr(out["means2d"]),
+                                  _dptr(out["conic_opacity"]), _dptr(out["color_tau"]),
+                                  _dptr(out["depth"]), _stream_ptr(stream)))
+        return out
+
+    def _image(self, out):
+        import torch
+        if out is None:
+            p = self.panel
+            out = torch.empty((p.height, p.width, 3), dtype=torch.float32, device="cuda")
+        return out
+
+    def render_projected(self, attrs, out=None, stream=None) -> Tuple[object, Dict]:
+        M = int(attrs["depth"].shape[1])
+        out = self._image(out)
+        st = CStats()
+        _check(load().lfd_render_projected(
+            self._h, M, _dptr(attrs["means2d"]), _dptr(attrs["conic_opacity"]),
+            _dptr(attrs["color_tau"]), _dptr(attrs["depth"]), _dptr(out),
+            _stream_ptr(stream), ct.byref(st)))
+        return out, st.as_dict()
+
+    def render(self, scene, cams: np.ndarray, out=None, stream=None) -> Tuple[object, Dict]:
+        out = self._image(out)
+        g = gaussians_struct(scene)
+        carr, n = cameras_array(cams)
+        st = CStats()
+        _check(load().lfd_render(self._h, ct.byref(g), carr, n, _dptr(out), _stream_ptr(stream),
+                                 ct.byref(st)))
+        return out, st.as_dict()
+
+    def render_host(self, scene_host, cams: np.ndarray, out_host, stream=None):
+        """scene_host / out_host: contiguous CPU tensors (pinned for speed)."""
+        g = gaussians_struct(scene_host, host=True)
+        carr, n = cameras_array(cams)
+        st = CStats()
+        _check(load().lfd_render_host(self._h, ct.byref(g), carr, n, out_host.data_ptr(),
+                                      _stream_ptr(stream), ct.byref(st)))
+        return out_host, st.as_dict()
+
+    def stage_totals(self, reset: bool = False) -> Dict[str, float]:
+        t = CStageTotals()
+        _check(load().lfd_get_stage_totals(self._h, ct.byref(t), 1 if reset else 0))
+        return {f: getattr(t, f) for f, _ in t._fields_}
+
+    def lists(self, num_pairs: int, with_keys: bool = False):
+        lst = np.zeros(max(num_pairs, 1), np.uint32)
+        ranges = np.zeros((self.T, self.K, 2), np.uint32)
+        keys = np.zeros(max(num_pairs, 1), np.uint64) if with_keys else None
+        _check(load().lfd_plan_copy_lists(self._h, lst.ctypes.data, ranges.ctypes.data,
+                                          keys.ctypes.data if with_keys else None,
+                                          max(num_pairs, 1)))
+        return lst[:num_pairs], ranges, (keys[:num_pairs] if with_keys else None)
+
+
+def kernel_launches() -> int:
+    """Kernels launched by liblfd in this process so far."""
+    return int(load().lfd_kernel_launches())
+
+
+def scene_to_device(scene: Dict[str, np.ndarray], device="cuda", dtype=None):
+    import torch
+    out = {}
+    for k, v in scene.items():
+        out[k] = torch.from_numpy(np.ascontiguousarray(v, dtype=np.float32)).to(device)
+    return out

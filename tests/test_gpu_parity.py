@@ -1,0 +1,319 @@
+"""Parity of the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Bit-exact: view index V, remap table Psi and its cluster runs, tile bins,
+Eq. 11 keys, the sorted list and the range table. Tolerance (clamped [0, 1]
+images): max |err| <= 2e-3 and at most 0.1 % of subpixels off by more than
+1/255, against the FP64 oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_04509_gb300 import synth
+
+from .helpers import assert_image_close, image_metrics
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU-only containers
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2605_04509_gb300 import lfd  # noqa: E402
+
+
+def f32_attrs(proj, c):
+    """Oracle FP64 projection rounded to the float32 stage layouts."""
+    means = oracle.means_by_slot(proj["mean2d"], proj["vvalid"], c).astype(np.float32)
+    K, M = proj["depth"].shape
+    co = np.zeros((K, M, 4), np.float32)
+    co[..., :3] = proj["conic"]
+    co[..., 3] = proj["opac"][None, :]
+    ct_ = np.zeros((K, M, 4), np.float32)
+    ct_[..., :3] = proj["color"]
+    ct_[..., 3] = np.where(proj["valid"].astype(bool), proj["tau"], -1.0)
+    return {"means2d": np.ascontiguousarray(means), "conic_opacity": co, "color_tau": ct_,
+            "depth": proj["depth"].astype(np.float32)}
+
+
+def to_dev(attrs):
+    return {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in attrs.items()}
+
+
+def oracle_proj_from_f32(attrs, num_views, c):
+    """The float32 stage inputs as an FP64 oracle projection dict."""
+    mean2d, vvalid = oracle.per_view_from_slots(attrs["means2d"].astype(np.float64), num_views, c)
+    tau = attrs["color_tau"][..., 3].astype(np.float64)
+    return {"mean2d": mean2d, "vvalid": vvalid,
+            "conic": np.ascontiguousarray(attrs["conic_opacity"][..., :3], dtype=np.float64),
+            "color": np.ascontiguousarray(attrs["color_tau"][..., :3], dtype=np.float64),
+            "opac": np.ascontiguousarray(attrs["conic_opacity"][0, :, 3], dtype=np.float64),
+            "depth": attrs["depth"].astype(np.float64),
+            "valid": (tau >= 0).astype(np.uint8)}
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    w = synth.WORKLOADS["tiny"]
+    scene = synth.scene_for(w)
+    cams = synth.arc_cameras(w.rig, w.panel.width, w.panel.height)
+    return w, scene, cams
+
+
+PANELS = [
+    synth.WORKLOADS["tiny"].panel,
+    synth.Panel(250, 141, 13, 0.2027, 5.3, 0.7),
+    synth.Panel(64, 40, 1, 0.0, 4.0, 0.0),
+    synth.Panel(97, 33, 255, -0.31, 7.7, -2.5),
+]
+
+
+@pytest.mark.parametrize("panel", PANELS)
+@pytest.mark.parametrize("tile,c", [((16, 16), 8), ((8, 8), 1), ((32, 16), 3)])
+def test_panel_tables_bit_exact(panel, tile, c):
+    plan = lfd.Plan(panel, tile=tile, views_per_cluster=c)
+    V, psi, n_sub, seg = plan.tables()
+    Vo = oracle.view_index(panel)
+    np.testing.assert_array_equal(V, Vo)
+    po, no, so = oracle.remap(Vo, panel.num_views, tile[0], tile[1], c)
+    np.testing.assert_array_equal(n_sub, no)
+    np.testing.assert_array_equal(seg, so)
+    for t in range(len(n_sub)):
+        np.testing.assert_array_equal(psi[t, : n_sub[t]], po[t, : no[t]])
+    plan.close()
+
+
+def test_panel_tables_paper_4k():
+    panel = synth.WORKLOADS["paper4k"].panel
+    plan = lfd.Plan(panel, tile=(16, 16), views_per_cluster=8)
+    V, psi, n_sub, seg = plan.tables()
+    Vo = oracle.view_index(panel)
+    np.testing.assert_array_equal(V, Vo)
+    po, no, so = oracle.remap(Vo, panel.num_views, 16, 16, 8)
+    np.testing.assert_array_equal(seg, so)
+    np.testing.assert_array_equal(psi, np.where(np.arange(psi.shape[1])[None] < no[:, None], po, psi))
+    plan.close()
+
+
+@pytest.mark.parametrize("c", [1, 3, 8])
+def test_projection_matches_fp64(tiny, c):
+    w, scene, cams = tiny
+    plan = lfd.Plan(w.panel, views_per_cluster=c)
+    out = plan.project(lfd.scene_to_device(scene), cams)
+    torch.cuda.synchronize()
+    got = {k: v.cpu().numpy() for k, v in out.items()}
+    proj = oracle.project(scene, cams, w.panel.width, w.panel.height, c)
+    ref = f32_attrs(proj, c)
+    gm, rm = got["means2d"], ref["means2d"]
+    assert np.array_equal(np.isnan(gm), np.isnan(rm))
+    fin = np.isfinite(rm)
+    np.testing.assert_allclose(gm[fin], rm[fin], rtol=0, atol=2e-3)
+    valid = ref["color_tau"][..., 3] >= 0
+    assert np.array_equal(got["color_tau"][..., 3] >= 0, valid)
+    gc, rc = got["conic_opacity"][valid][:, :3], ref["conic_opacity"][valid][:, :3]
+    scale = np.abs(rc).max(axis=1, keepdims=True)
+    assert (np.abs(gc - rc) <= 1e-4 * scale + 1e-7).all()
+    np.testing.assert_allclose(got["depth"][valid], ref["depth"][valid], rtol=1e-6)
+    np.testing.assert_allclose(got["color_tau"][valid][:, :3], ref["color_tau"][valid][:, :3],
+                               atol=2e-5)
+    np.testing.assert_allclose(got["color_tau"][valid][:, 3], ref["color_tau"][valid][:, 3],
+                               atol=2e-5)
+    plan.close()
+
+
+def _stage_inputs(w, scene, cams, c):
+    proj = oracle.project(scene, cams, w.panel.width, w.panel.height, c)
+    return f32_attrs(proj, c)
+
+
+@pytest.mark.parametrize("sort_mode", [lfd.SORT_DEPTH_FIRST, lfd.SORT_KEY64])
+@pytest.mark.parametrize("tile,c", [((16, 16), 8), ((8, 8), 1), ((32, 16), 3), ((16, 8), 5)])
+def test_bins_sort_ranges_bit_exact(tiny, sort_mode, tile, c):
+    w, scene, cams = tiny
+    attrs = _stage_inputs(w, scene, cams, c)
+    plan = lfd.Plan(w.panel, tile=tile, views_per_cluster=c, sort_mode=sort_mode)
+    _img, st = plan.render_projected(to_dev(attrs))
+    ref = oracle.mirror_lists(w.panel.width, w.panel.height, tile,
+                              attrs["conic_opacity"][..., :3], attrs["color_tau"][..., 3],
+                              attrs["depth"], attrs["means2d"])
+    assert st["num_pairs"] == len(ref["list"]) > 1000
+    lst, ranges, keys = plan.lists(st["num_pairs"], with_keys=sort_mode == lfd.SORT_KEY64)
+    np.testing.assert_array_equal(ranges, ref["ranges"])
+    np.testing.assert_array_equal(lst, ref["list"])
+    if keys is not None:
+        np.testing.assert_array_equal(keys, ref["keys_sorted"])
+    plan.close()
+
+
+def test_bins_random_conics_bit_exact():
+    # synthetic ellipses of every orientation and size, many off-panel
+    panel = synth.Panel(200, 120, 12, 0.15, 5.0, 0.0)
+    K, M, C = 3, 3000, 4
+    rng = np.random.default_rng(31)
+    conic = synth.random_conics(K * M, 32, 0.6, 30.0).reshape(K, M, 3)
+    tau = rng.uniform(0, 11.0, (K, M)).astype(np.float32)
+    tau[rng.uniform(size=(K, M)) < 0.1] = -1.0
+    depth = rng.uniform(0.3, 40.0, (K, M)).astype(np.float32)
+    base = np.stack([rng.uniform(-40, 240, (K, M)), rng.uniform(-40, 160, (K, M))], -1)
+    means = (base[:, :, None, :] + rng.normal(0, 10.0, (K, M, C, 2))).astype(np.float32)
+    means[rng.uniform(size=(K, M, C)) < 0.05] = np.nan
+    co = np.concatenate([conic, np.full((K, M, 1), 0.5, np.float32)], -1)
+    ct_ = np.concatenate([np.full((K, M, 3), 0.5, np.float32), tau[..., None]], -1)
+    attrs = {"means2d": means, "conic_opacity": co, "color_tau": ct_, "depth": depth}
+    for sort_mode in (lfd.SORT_DEPTH_FIRST, lfd.SORT_KEY64):
+        plan = lfd.Plan(panel, tile=(16, 16), views_per_cluster=C, sort_mode=sort_mode)
+        _img, st = plan.render_projected(to_dev(attrs))
+        ref = oracle.mirror_lists(panel.width, panel.height, (16, 16), conic, tau, depth, means)
+        lst, ranges, keys = plan.lists(st["num_pairs"], with_keys=sort_mode == lfd.SORT_KEY64)
+        assert st["num_pairs"] == len(ref["list"])
+        np.testing.assert_array_equal(lst, ref["list"])
+        np.testing.assert_array_equal(ranges, ref["ranges"])
+        if keys is not None:
+            np.testing.assert_array_equal(keys, ref["keys_sorted"])
+        plan.close()
+
+
+@pytest.mark.parametrize("c", [1, 4, 8])
+def test_blend_matches_oracle_on_same_lists(tiny, c):
+    w, scene, cams = tiny
+    attrs = _stage_inputs(w, scene, cams, c)
+    plan = lfd.Plan(w.panel, views_per_cluster=c)
+    plan.set_flags(lfd.FLAG_COUNT_EVALS)
+    img, st = plan.render_projected(to_dev(attrs))
+    ref = oracle.mirror_lists(w.panel.width, w.panel.height, (16, 16),
+                              attrs["conic_opacity"][..., :3], attrs["color_tau"][..., 3],
+                              attrs["depth"], attrs["means2d"])
+    p64 = oracle_proj_from_f32(attrs, w.panel.num_views, c)
+    V = oracle.view_index(w.panel)
+    want, n_eval = oracle.blend_lists(p64, V, c, ref["ranges"], ref["list"])
+    m = assert_image_close(img.cpu().numpy(), want, f"blend C={c}")
+    assert m["psnr"] > 60
+    # the GPU's count of visited list entries agrees with the oracle's walk
+    assert abs(st["num_evals"] - n_eval) <= 1e-3 * n_eval
+    plan.close()
+
+
+@pytest.mark.parametrize("c", [1, 3, 8])
+@pytest.mark.parametrize("sort_mode", [lfd.SORT_DEPTH_FIRST, lfd.SORT_KEY64])
+def test_render_matches_fp64_oracle(tiny, c, sort_mode):
+    w, scene, cams = tiny
+    plan = lfd.Plan(w.panel, views_per_cluster=c, sort_mode=sort_mode)
+    img, st = plan.render(lfd.scene_to_device(scene), cams)
+    proj = oracle.project(scene, cams, w.panel.width, w.panel.height, c)
+    V = oracle.view_index(w.panel)
+    ref, _ = oracle.render(proj, V, c, mode=1)
+    m = assert_image_close(img.cpu().numpy(), ref, f"render C={c}")
+    assert m["psnr"] > 60 and st["num_pairs"] > 0
+    plan.close()
+
+
+@pytest.mark.parametrize("tile", [(8, 8), (32, 16), (16, 8)])
+def test_render_ragged_panel(tile):
+    panel = synth.Panel(250, 141, 13, 0.2027, 5.3, 0.7)
+    rig = synth.Rig(13, 40.0, 4.0, 50.0)
+    scene = synth.uniform_scene(1500, 77)
+    cams = synth.arc_cameras(rig, panel.width, panel.height)
+    plan = lfd.Plan(panel, tile=tile, views_per_cluster=4)
+    img, _ = plan.render(lfd.scene_to_device(scene), cams)
+    proj = oracle.project(scene, cams, panel.width, panel.height, 4)
+    ref, _ = oracle.render(proj, oracle.view_index(panel), 4, mode=1)
+    assert_image_close(img.cpu().numpy(), ref, f"ragged {tile}")
+    plan.close()
+
+
+def test_edge_cases(tiny):
+    w, scene, cams = tiny
+    bg = (0.1, 0.2, 0.3)
+    # no Gaussians: background everywhere
+    plan = lfd.Plan(w.panel, views_per_cluster=8, bg=bg)
+    empty = {k: v[:0] for k, v in scene.items()}
+    img, st = plan.render(lfd.scene_to_device(empty), cams)
+    assert st["num_pairs"] == 0
+    np.testing.assert_array_equal(img.cpu().numpy(), np.broadcast_to(np.float32(bg), img.shape))
+    # everything behind every camera
+    behind = dict(scene)
+    behind["means"] = (scene["means"] * 0.01 + np.float32([0, 0, -50])).astype(np.float32)
+    img, st = plan.render(lfd.scene_to_device(behind), cams)
+    assert st["num_pairs"] == 0
+    np.testing.assert_array_equal(img.cpu().numpy(), np.broadcast_to(np.float32(bg), img.shape))
+    plan.close()
+    # one view (plain 3DGS) and one cluster holding every view
+    for panel, c, nv in ((synth.Panel(128, 72, 1, 0.2, 5.0), 1, 1),
+                         (synth.Panel(128, 72, 6, 0.2, 5.0), 8, 6)):
+        rig = synth.Rig(nv, 20.0, 4.0, 50.0)
+        cm = synth.arc_cameras(rig, panel.width, panel.height)
+        sc = synth.uniform_scene(800, 5)
+        plan = lfd.Plan(panel, views_per_cluster=c)
+        img, _ = plan.render(lfd.scene_to_device(sc), cm)
+        proj = oracle.project(sc, cm, panel.width, panel.height, c)
+        ref, _ = oracle.render(proj, oracle.view_index(panel), c, mode=1)
+        assert_image_close(img.cpu().numpy(), ref, f"N={nv} C={c}")
+        plan.close()
+
+
+def test_deterministic(tiny):
+    w, scene, cams = tiny
+    plan = lfd.Plan(w.panel, views_per_cluster=8)
+    s = lfd.scene_to_device(scene)
+    a, _ = plan.render(s, cams)
+    a = a.clone()
+    b, _ = plan.render(s, cams)
+    assert torch.equal(a, b)
+    plan.close()
+
+
+def test_host_entry_point_matches_device(tiny):
+    w, scene, cams = tiny
+    plan = lfd.Plan(w.panel, views_per_cluster=8)
+    dev, _ = plan.render(lfd.scene_to_device(scene), cams)
+    host_scene = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in scene.items()}
+    out = torch.empty(dev.shape, dtype=torch.float32).pin_memory()
+    plan.render_host(host_scene, cams, out)
+    assert torch.equal(out, dev.cpu())
+    plan.close()
+
+
+def test_invalid_arguments(tiny):
+    w, scene, cams = tiny
+    with pytest.raises(lfd.LFDError) as e:
+        lfd.Plan(synth.Panel(0, 10, 8, 0.1, 4.0))
+    assert e.value.status == lfd.LFD_ERR_INVALID
+    with pytest.raises(lfd.LFDError):
+        lfd.Plan(w.panel, tile=(64, 64))
+    with pytest.raises(lfd.LFDError):
+        lfd.Plan(w.panel, views_per_cluster=0)
+    plan = lfd.Plan(w.panel, views_per_cluster=8)
+    with pytest.raises(lfd.LFDError) as e:
+        plan.render(lfd.scene_to_device(scene), cams[:3])
+    assert e.value.status == lfd.LFD_ERR_INVALID
+    plan.close()
+
+
+@pytest.mark.slow
+def test_paper4k_sampled_crops():
+    # The paper-scale workload at full size, in the launch configuration the
+    # benchmark times; the oracle recomputes sampled 16x16 crops by definition.
+    w = synth.WORKLOADS["paper4k"]
+    scene = synth.scene_for(w)
+    cams = synth.arc_cameras(w.rig, w.panel.width, w.panel.height)
+    c = 8
+    plan = lfd.Plan(w.panel, tile=(16, 16), views_per_cluster=c)
+    img, st = plan.render(lfd.scene_to_device(scene), cams)
+    got = img.cpu().numpy()
+    assert st["num_pairs"] > 10_000_000
+    proj = oracle.project(scene, cams, w.panel.width, w.panel.height, c)
+    V = oracle.view_index(w.panel)
+    # crops: the densest region, the panel centre, random places, the edge
+    dens = np.clip(got, 0, 1).sum(-1)
+    yy, xx = np.unravel_index(np.argmax(dens), dens.shape)
+    rng = np.random.default_rng(8)
+    crops = [(min(xx // 16, 239) * 16, min(yy // 16, 134) * 16), (1920, 1072), (3824, 2144)]
+    crops += [(int(rng.integers(0, 240)) * 16, int(rng.integers(0, 135)) * 16) for _ in range(3)]
+    worst = None
+    for x0, y0 in crops:
+        crop = (x0, y0, x0 + 16, y0 + 16)
+        ref, _ = oracle.render(proj, V, c, crop=crop, mode=1)
+        m = image_metrics(got[y0:y0 + 16, x0:x0 + 16], ref)
+        worst = m if worst is None or m["max_err"] > worst["max_err"] else worst
+        assert_image_close(got[y0:y0 + 16, x0:x0 + 16], ref, f"crop {crop}")
+    plan.close()
