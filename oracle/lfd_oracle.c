@@ -171,6 +171,21 @@ static void load_cam(const float *c, cam64 *o) {
   o->cy = c[15];
 }
 
+/* View-space depth in FP32, each operation rounded in this fixed order:
+ * ((R20 mx + R21 my) + R22 mz) + t2. Eq. 11 stores the depth of the sort
+ * key as the bits of a 32-bit float, so the depth order (and with it the
+ * near-plane test) is decided in FP32 by this one sequence; everything else
+ * in the oracle stays FP64. */
+static float depth_f32(const float *cam, const float *m) {
+  const float a0 = cam[6] * m[0];
+  const float a1 = cam[7] * m[1];
+  const float a2 = cam[8] * m[2];
+  float d = a0 + a1;
+  d = d + a2;
+  d = d + cam[11];
+  return d;
+}
+
 static void to_camera(const cam64 *c, const double m[3], double p[3]) {
   for (int r = 0; r < 3; ++r)
     p[r] = c->R[3 * r + 0] * m[0] + c->R[3 * r + 1] * m[1] +
@@ -232,7 +247,7 @@ int orc_project(int64_t M, const float *means, const float *scales,
       double p[3];
       to_camera(&cv[j], m, p);
       const size_t o = (size_t)j * M + i;
-      if (p[2] > NEAR_PLANE) {
+      if (depth_f32(cams + 16 * j, means + 3 * i) > (float)NEAR_PLANE) {
         vvalid[o] = 1;
         mean2d[2 * o] = cv[j].fx * p[0] / p[2] + cv[j].cx;
         mean2d[2 * o + 1] = cv[j].fy * p[1] / p[2] + cv[j].cy;
@@ -279,9 +294,10 @@ int orc_project(int64_t M, const float *means, const float *scales,
       valid[ok] = 0;
       conic[3 * ok] = conic[3 * ok + 1] = conic[3 * ok + 2] = 0.0;
       color[3 * ok] = color[3 * ok + 1] = color[3 * ok + 2] = 0.0;
-      depth[ok] = p[2];
+      const float zkey = depth_f32(cams + 16 * jr, means + 3 * i);
+      depth[ok] = (double)zkey;
       tau[ok] = -1.0;
-      if (!(p[2] > NEAR_PLANE)) continue;
+      if (!(zkey > (float)NEAR_PLANE)) continue;
       /* Jacobian of the pinhole projection, with the 3DGS clamp of x/z and
        * y/z to 1.3 times the half field of view. */
       const double limx = 1.3 * (0.5 * (double)W / cr->fx);

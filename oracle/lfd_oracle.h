@@ -42,7 +42,10 @@ int orc_clusters(int N, int C, int32_t *slot_view, int32_t *rep);
 
 /* Eq. 4-6 in FP64. Outputs: per-view means [N][M][2] and validity [N][M];
  * per-cluster conic [K][M][3], depth [K][M], colour [K][M][3],
- * tau = 2 ln(255 o) [K][M] and validity [K][M]. */
+ * tau = 2 ln(255 o) [K][M] and validity [K][M]. The depth (and the
+ * near-plane test z > 0.2) is the one FP32 quantity: Eq. 11 keys order by the
+ * bits of a 32-bit float depth, so it is evaluated as
+ * ((R20 mx + R21 my) + R22 mz) + t2 with every operation rounded to float. */
 int orc_project(int64_t M, const float *means, const float *scales,
                 const float *quats, const float *opac, const float *sh,
                 int sh_degree, int N, const float *cams, int W, int H, int C,

@@ -106,7 +106,8 @@ def test_covariance_matches_finite_difference_jacobian():
             S3 = Rq @ np.diag(scales[i].astype(np.float64) ** 2) @ Rq.T
             S2 = J @ R @ S3 @ R.T @ J.T + 0.3 * np.eye(2)
             np.testing.assert_allclose(_conic_to_cov(p["conic"][j, i]), S2, rtol=1e-6, atol=1e-9)
-            assert p["depth"][j, i] == pytest.approx(pc[2], rel=1e-12)
+            # the depth is kept in FP32 (the precision of the Eq. 11 key)
+            assert p["depth"][j, i] == pytest.approx(pc[2], rel=3e-7)
 
 
 def test_jacobian_clamp_off_screen():
