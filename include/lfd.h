@@ -87,7 +87,7 @@ extern "C" {
 
 /* lfd_set_flags() bits */
 #define LFD_FLAG_STAGE_TIMING 1 /* fill lfd_stats.ms_* (adds host syncs)  */
-#define LFD_FLAG_COUNT_EVALS 2  /* fill lfd_stats.num_evals              */
+#define LFD_FLAG_COUNT_EVALS 2  /* fill lfd_stats.num_visits, num_evals  */
 
 typedef struct lfd_plan lfd_plan;
 
@@ -130,7 +130,11 @@ typedef struct {
 
 typedef struct {
   int64_t num_pairs;  /* P: Gaussian-(tile, cluster) pairs of the last frame */
-  int64_t num_evals;  /* E: list entries visited by all subpixels (flag)    */
+  int64_t num_visits; /* list entries walked by all subpixels until they
+                         saturate or the list ends (flag)                   */
+  int64_t num_evals;  /* E: of those, entries whose region in the
+                         subpixel's own view meets the tile, for which the
+                         Eq. 10 opacity was evaluated (flag)                 */
   float ms_project, ms_keygen, ms_sort, ms_blend; /* stage times (flag)    */
 } lfd_stats;
 

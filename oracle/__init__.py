@@ -80,6 +80,8 @@ def _declare(L):
         f = getattr(L, name)
         f.argtypes = args
         f.restype = _I
+    L.orc_set_alpha_min.argtypes = [_D]
+    L.orc_set_alpha_min.restype = _D
 
 
 def _ptr(a: np.ndarray):
@@ -94,6 +96,33 @@ def _check(rc: int, what: str):
 
 def num_threads() -> int:
     return lib().orc_num_threads()
+
+
+class alpha_min:
+    """Context manager rendering with a different alpha skip threshold."""
+
+    def __init__(self, value: float):
+        self.value = value
+        self.old = None
+
+    def __enter__(self):
+        self.old = lib().orc_set_alpha_min(float(self.value))
+        return self
+
+    def __exit__(self, *exc):
+        lib().orc_set_alpha_min(self.old)
+        return False
+
+
+def render_bracket(proj, V, c, crop=None, rel: float = 1e-3, **kw):
+    """The definition rendered at the 1/255 threshold and at (1 -/+ rel) of it;
+    returns (image, lower-threshold image, upper-threshold image)."""
+    ref, _ = render(proj, V, c, crop=crop, **kw)
+    with alpha_min(ALPHA_MIN * (1 - rel)):
+        lo, _ = render(proj, V, c, crop=crop, **kw)
+    with alpha_min(ALPHA_MIN * (1 + rel)):
+        hi, _ = render(proj, V, c, crop=crop, **kw)
+    return ref, lo, hi
 
 
 def num_clusters(n: int, c: int) -> int:

@@ -38,9 +38,18 @@
 
 #define NEAR_PLANE 0.2
 #define DILATION 0.3
-#define ALPHA_MIN (1.0 / 255.0)
+/* skip threshold of Eq. 10's alpha (3DGS: 1/255); settable for sensitivity
+ * analysis of the definition, see orc_set_alpha_min */
+static double g_alpha_min = 1.0 / 255.0;
+#define ALPHA_MIN g_alpha_min
 #define ALPHA_MAX 0.99
 #define T_MIN 1e-4
+
+double orc_set_alpha_min(double v) {
+  const double old = g_alpha_min;
+  if (v > 0.0) g_alpha_min = v;
+  return old;
+}
 
 int orc_num_threads(void) {
 #ifdef _OPENMP
@@ -640,7 +649,7 @@ int orc_render_fullframe(int W, int H, int N, const uint8_t *V, int64_t M,
 /* is float32, each operation correctly rounded, in the order written.  */
 /* ------------------------------------------------------------------ */
 typedef struct {
-  float a, b, c, tau, det, hx, hy, ys;
+  float a, b, c, tau, det, hx, hy, ys, ia;
 } binq;
 
 static int bin_prep(float a, float b, float c, float tau, binq *o) {
@@ -662,6 +671,7 @@ static int bin_prep(float a, float b, float c, float tau, binq *o) {
   const float dc = det * c;
   const float r = sqrtf(tau / dc);
   o->ys = b * r;
+  o->ia = 1.0f / a;
   return 1;
 }
 
@@ -714,8 +724,8 @@ static int bin_row(const binq *g, const binv *v, int ty, int TW, int TH,
   const float wR = sqrtf(fmaxf(at - eR * dR, 0.0f));
   const float eL = g->det * dL;
   const float wL = sqrtf(fmaxf(at - eL * dL, 0.0f));
-  const float xR = v->mx + ((wR - g->b * dR) / g->a);
-  const float xL = v->mx + ((-wL - g->b * dL) / g->a);
+  const float xR = v->mx + ((wR - g->b * dR) * g->ia);
+  const float xL = v->mx + ((-wL - g->b * dL) * g->ia);
   const float fx0 = fmaxf(ceilf(xL - 0.5f), v->bx0);
   const float fx1 = fminf(floorf(xR - 0.5f), v->bx1);
   if (!(fx0 <= fx1)) return 0;

@@ -103,6 +103,12 @@ int orc_mirror_sort(int64_t P, uint64_t *keys, uint32_t *vals);
 int orc_mirror_ranges(int64_t P, const uint64_t *keys_sorted, int bit_k,
                       int T, int K, uint32_t *ranges);
 
+/* Set the alpha skip threshold used by the blends (default 1/255, the 3DGS
+ * rule) and return the previous one; v <= 0 leaves it unchanged. The
+ * definition is discontinuous at this threshold: tests render it slightly
+ * above and below to find the subpixels where the result itself jumps. */
+double orc_set_alpha_min(double v);
+
 int orc_num_threads(void);
 
 #ifdef __cplusplus

@@ -19,7 +19,7 @@ namespace lfd {
 namespace {
 
 struct BinQ {
-  float a, b, c, tau, det, hx, hy, ys;
+  float a, b, c, tau, det, hx, hy, ys, ia;
 };
 
 struct BinV {
@@ -47,6 +47,7 @@ __device__ __forceinline__ bool bin_prep(float a, float b, float c, float tau, B
   const float dc = __fmul_rn(det, c);
   const float r = __fsqrt_rn(__fdiv_rn(tau, dc));
   g.ys = __fmul_rn(b, r);
+  g.ia = __fdiv_rn(1.f, a);
   return true;
 }
 
@@ -93,8 +94,8 @@ __device__ __forceinline__ bool bin_row(const BinQ& g, const BinV& v, int ty, in
   const float wR = __fsqrt_rn(fmaxf(__fsub_rn(at, __fmul_rn(eR, dR)), 0.f));
   const float eL = __fmul_rn(g.det, dL);
   const float wL = __fsqrt_rn(fmaxf(__fsub_rn(at, __fmul_rn(eL, dL)), 0.f));
-  const float xR = __fadd_rn(v.mx, __fdiv_rn(__fsub_rn(wR, __fmul_rn(g.b, dR)), g.a));
-  const float xL = __fadd_rn(v.mx, __fdiv_rn(__fsub_rn(-wL, __fmul_rn(g.b, dL)), g.a));
+  const float xR = __fadd_rn(v.mx, __fmul_rn(__fsub_rn(wR, __fmul_rn(g.b, dR)), g.ia));
+  const float xL = __fadd_rn(v.mx, __fmul_rn(__fsub_rn(-wL, __fmul_rn(g.b, dL)), g.ia));
   const float fx0 = fmaxf(ceilf(__fsub_rn(xL, 0.5f)), v.bx0);
   const float fx1 = fminf(floorf(__fsub_rn(xR, 0.5f)), v.bx1);
   if (!(fx0 <= fx1)) return false;
@@ -103,12 +104,14 @@ __device__ __forceinline__ bool bin_row(const BinQ& g, const BinV& v, int ty, in
   return true;
 }
 
-// Walk the union of the cluster's tiles in ascending tile id, 64 tile
-// columns at a time per tile row; calls emit(t) per tile, returns the count.
-template <typename Emit>
-__device__ __forceinline__ uint32_t bin_union(const PanelGeom& pg, const BinQ& q,
-                                              const float2* __restrict__ means, Emit emit) {
-  int ty0 = INT_MAX, ty1 = -1, c0 = INT_MAX, c1 = -1;
+// Row and tile-column range of the cluster's union (bounding boxes).
+__device__ __forceinline__ void bin_extent(const PanelGeom& pg, const BinQ& q,
+                                           const float2* __restrict__ means, int& ty0, int& ty1,
+                                           int& c0, int& c1) {
+  ty0 = INT_MAX;
+  ty1 = -1;
+  c0 = INT_MAX;
+  c1 = -1;
   for (int l = 0; l < pg.C; ++l) {
     const float2 m = means[l];
     BinV v;
@@ -119,6 +122,15 @@ __device__ __forceinline__ uint32_t bin_union(const PanelGeom& pg, const BinQ& q
     c0 = min(c0, (int)v.bx0 / pg.TW);
     c1 = max(c1, (int)v.bx1 / pg.TW);
   }
+}
+
+// The union of the cluster's tiles, row by row and 64 tile columns at a time:
+// on_mask(ty, w0, mask) gets the tiles w0 + bit of row ty, rows and windows in
+// ascending order. Returns the tile count.
+template <typename OnMask>
+__device__ __forceinline__ uint32_t bin_rows(const PanelGeom& pg, const BinQ& q,
+                                             const float2* __restrict__ means, int ty0, int ty1,
+                                             int c0, int c1, OnMask on_mask) {
   uint32_t n = 0;
   for (int ty = ty0; ty <= ty1; ++ty) {
     for (int w0 = c0; w0 <= c1; w0 += 64) {
@@ -137,15 +149,37 @@ __device__ __forceinline__ uint32_t bin_union(const PanelGeom& pg, const BinQ& q
         mask |= bits << (a - w0);
       }
       n += __popcll(mask);
-      while (mask) {
-        const int bit = __ffsll((long long)mask) - 1;
-        mask &= mask - 1ull;
-        emit(ty * pg.TX + w0 + bit);
-      }
+      on_mask(ty, w0, mask);
     }
   }
   return n;
 }
+
+// Walk the union of the cluster's tiles in ascending tile id; calls emit(t).
+template <typename Emit>
+__device__ __forceinline__ uint32_t bin_union(const PanelGeom& pg, const BinQ& q,
+                                              const float2* __restrict__ means, Emit emit) {
+  int ty0, ty1, c0, c1;
+  bin_extent(pg, q, means, ty0, ty1, c0, c1);
+  return bin_rows(pg, q, means, ty0, ty1, c0, c1, [&](int ty, int w0, unsigned long long mask) {
+    while (mask) {
+      const int bit = __ffsll((long long)mask) - 1;
+      mask &= mask - 1ull;
+      emit(ty * pg.TX + w0 + bit);
+    }
+  });
+}
+
+// Compact record of an item's union written by the count pass so that the
+// emit pass need not redo the geometry: header = ty0 | c0 << 16 | rows << 32
+// | overflow << 40, then one 64-tile mask per row. Items whose union spans
+// more than kDescRows rows or 64 tile columns are marked overflow and redone.
+constexpr int kDescRows = 7;
+struct __align__(16) BinDesc {
+  unsigned long long header;
+  unsigned long long mask[kDescRows];
+};
+static_assert(sizeof(BinDesc) == kBinDescBytes, "descriptor size");
 
 __global__ void k_item_keys(PanelGeom g, int64_t M, const float* __restrict__ depth,
                             const float4* __restrict__ color_tau, uint64_t* __restrict__ keys,
@@ -162,16 +196,30 @@ __global__ void k_item_keys(PanelGeom g, int64_t M, const float* __restrict__ de
 __global__ void k_bin_count(PanelGeom g, int64_t M, const float2* __restrict__ means2d,
                             const float4* __restrict__ conic_opacity,
                             const float4* __restrict__ color_tau, const uint32_t* __restrict__ order,
-                            int64_t n_items, uint32_t* __restrict__ counts) {
+                            int64_t n_items, uint32_t* __restrict__ counts,
+                            BinDesc* __restrict__ desc) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n_items) return;
   const uint32_t r = order ? order[s] : (uint32_t)s;
   const float4 co = conic_opacity[r];
   BinQ q;
   uint32_t n = 0;
-  if (bin_prep(co.x, co.y, co.z, color_tau[r].w, q))
-    n = bin_union(g, q, means2d + (size_t)r * g.C, [](int) {});
+  unsigned long long header = 0ull;
+  if (bin_prep(co.x, co.y, co.z, color_tau[r].w, q)) {
+    const float2* means = means2d + (size_t)r * g.C;
+    int ty0, ty1, c0, c1;
+    bin_extent(g, q, means, ty0, ty1, c0, c1);
+    const int rows = ty1 >= ty0 ? ty1 - ty0 + 1 : 0;
+    const bool fits = rows <= kDescRows && (rows == 0 || c1 - c0 < 64);
+    n = bin_rows(g, q, means, ty0, ty1, c0, c1, [&](int ty, int, unsigned long long mask) {
+      if (desc && fits) desc[s].mask[ty - ty0] = mask;
+    });
+    header = rows == 0 ? 0ull
+                       : ((unsigned long long)ty0 | ((unsigned long long)c0 << 16) |
+                          ((unsigned long long)rows << 32) | ((unsigned long long)(fits ? 0 : 1) << 40));
+  }
   counts[s] = n;
+  if (desc) desc[s].header = header;
 }
 
 __global__ void k_bin_emit(PanelGeom g, int64_t M, const float2* __restrict__ means2d,
@@ -179,16 +227,40 @@ __global__ void k_bin_emit(PanelGeom g, int64_t M, const float2* __restrict__ me
                            const float4* __restrict__ color_tau, const float* __restrict__ depth,
                            const uint32_t* __restrict__ order, int64_t n_items,
                            const uint32_t* __restrict__ offsets, uint32_t* __restrict__ keys32,
-                           uint64_t* __restrict__ keys64, uint32_t* __restrict__ vals) {
+                           uint64_t* __restrict__ keys64, uint32_t* __restrict__ vals,
+                           const BinDesc* __restrict__ desc) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n_items) return;
   const uint32_t r = order ? order[s] : (uint32_t)s;
-  const float4 co = conic_opacity[r];
-  BinQ q;
-  if (!bin_prep(co.x, co.y, co.z, color_tau[r].w, q)) return;
   const uint32_t k = (uint32_t)(r / M);
   const uint32_t i = (uint32_t)(r - (uint64_t)k * M);
   uint32_t pos = offsets[s];
+  if (desc) {
+    const unsigned long long h = desc[s].header;
+    if (!((h >> 40) & 1ull)) {
+      const int ty0 = (int)(h & 0xffffull), c0 = (int)((h >> 16) & 0xffffull);
+      const int rows = (int)((h >> 32) & 0xffull);
+      const uint64_t lo = keys64 ? (((uint64_t)k << 32) | __float_as_uint(depth[r])) : 0ull;
+      for (int rr = 0; rr < rows; ++rr) {
+        unsigned long long mask = desc[s].mask[rr];
+        while (mask) {
+          const int bit = __ffsll((long long)mask) - 1;
+          mask &= mask - 1ull;
+          const uint32_t t = (uint32_t)((ty0 + rr) * g.TX + c0 + bit);
+          if (keys64)
+            keys64[pos] = ((uint64_t)t << (32 + g.bit_k)) | lo;
+          else
+            keys32[pos] = (t << g.bit_k) | k;
+          vals[pos] = i;
+          ++pos;
+        }
+      }
+      return;
+    }
+  }
+  const float4 co = conic_opacity[r];
+  BinQ q;
+  if (!bin_prep(co.x, co.y, co.z, color_tau[r].w, q)) return;
   if (keys64) {
     const uint64_t lo = ((uint64_t)k << 32) | __float_as_uint(depth[r]);
     const int shift = 32 + g.bit_k;
@@ -239,13 +311,13 @@ cudaError_t launch_item_keys(const PanelGeom& g, int64_t M, const float* depth,
 
 cudaError_t launch_bin_count(const PanelGeom& g, int64_t M, const float* means2d,
                              const float* conic_opacity, const float* color_tau,
-                             const uint32_t* order, int64_t n_items, uint32_t* counts,
+                             const uint32_t* order, int64_t n_items, uint32_t* counts, void* desc,
                              cudaStream_t s) {
   if (n_items == 0) return cudaSuccess;
   k_bin_count<<<blocks_for(n_items, 128), 128, 0, s>>>(
       g, M, reinterpret_cast<const float2*>(means2d),
       reinterpret_cast<const float4*>(conic_opacity), reinterpret_cast<const float4*>(color_tau),
-      order, n_items, counts);
+      order, n_items, counts, reinterpret_cast<BinDesc*>(desc));
   note_launches(1);
   return cudaGetLastError();
 }
@@ -254,12 +326,12 @@ cudaError_t launch_bin_emit(const PanelGeom& g, int64_t M, const float* means2d,
                             const float* conic_opacity, const float* color_tau,
                             const float* depth, const uint32_t* order, int64_t n_items,
                             const uint32_t* offsets, uint32_t* keys32, uint64_t* keys64,
-                            uint32_t* vals, cudaStream_t s) {
+                            uint32_t* vals, const void* desc, cudaStream_t s) {
   if (n_items == 0) return cudaSuccess;
   k_bin_emit<<<blocks_for(n_items, 128), 128, 0, s>>>(
       g, M, reinterpret_cast<const float2*>(means2d),
       reinterpret_cast<const float4*>(conic_opacity), reinterpret_cast<const float4*>(color_tau),
-      depth, order, n_items, offsets, keys32, keys64, vals);
+      depth, order, n_items, offsets, keys32, keys64, vals, reinterpret_cast<const BinDesc*>(desc));
   note_launches(1);
   return cudaGetLastError();
 }

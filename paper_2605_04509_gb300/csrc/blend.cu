@@ -9,7 +9,13 @@
 // Gaussians (conic pre-scaled by log2(e), opacity, colour, and the 2D means
 // of every slot view of the cluster), and each thread blends its subpixels
 // against the staged batch; a block-wide vote ends the walk once every
-// subpixel has saturated. Grid order is cluster-major so that one cluster's
+// subpixel has saturated. While staging, each Gaussian gets a bit per slot
+// view telling whether that view's region (bounding box of q <= tau, one
+// pixel of margin) meets the tile, and per view the staged entries with that
+// bit set are compacted (warp ballots) into an index list; each subpixel walks
+// only its own view's list. The union over the cluster's views (Alg. 2) keeps
+// the other entries in the list, but they cannot reach alpha >= 1/255 for
+// this view, so skipping them leaves every result bit-identical. Grid order is cluster-major so that one cluster's
 // attributes stay resident in L2 while its tiles are blended.
 #include "lfd_internal.h"
 
@@ -30,10 +36,14 @@ __device__ __forceinline__ float ex2_approx(float x) {
 template <int R, bool COUNT>
 __global__ void __launch_bounds__(256) k_blend(PanelGeom g, BlendArgs a) {
   extern __shared__ float4 smem[];
-  const int NB = blockDim.x;
-  float4* s_co = smem;
-  float4* s_col = smem + NB;
-  float2* s_mean = reinterpret_cast<float2*>(smem + 2 * NB);
+  const int NB = blockDim.x;  // a multiple of 32
+  const int NW = NB >> 5;
+  const int C = g.C;
+  float4* s_co = smem;        // conic * (-log2(e) / 2, -log2(e), -log2(e) / 2), opacity
+  float4* s_col = smem + NB;  // colour
+  float2* s_mean = reinterpret_cast<float2*>(smem + 2 * NB);        // [NB][C]
+  uint16_t* s_idx = reinterpret_cast<uint16_t*>(s_mean + NB * C);   // [C][NB]
+  int* s_cnt = reinterpret_cast<int*>(s_idx + ((C * NB + 1) & ~1));  // [C][NW + 1]
 
   const int k = blockIdx.x / g.T;
   const int t = blockIdx.x - k * g.T;
@@ -42,12 +52,20 @@ __global__ void __launch_bounds__(256) k_blend(PanelGeom g, BlendArgs a) {
   if (n <= 0) return;
   const uint2 rg = a.ranges[(size_t)t * g.K + k];
   const int tx = t % g.TX, ty = t / g.TX;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  // pixel-centre box of the tile, widened by one pixel: a Gaussian whose
+  // region bounding box misses it has alpha < 1/255 on every subpixel here
+  const float bx0 = (float)(tx * g.TW) + 0.5f - 1.f;
+  const float bx1 = (float)min(tx * g.TW + g.TW, g.W) - 0.5f + 1.f;
+  const float by0 = (float)(ty * g.TH) + 0.5f - 1.f;
+  const float by1 = (float)min(ty * g.TH + g.TH, g.H) - 0.5f + 1.f;
 
   float px[R], py[R], T[R], acc[R];
   int slot[R], ch[R];
   int64_t oidx[R];
   bool act[R];
-  uint32_t cnt = 0;
+  unsigned long long n_visit = 0, n_eval = 0;
 #pragma unroll
   for (int m = 0; m < R; ++m) {
     const int r = threadIdx.x + m * NB;
@@ -68,7 +86,7 @@ __global__ void __launch_bounds__(256) k_blend(PanelGeom g, BlendArgs a) {
       const int x = tx * g.TW + xl, y = ty * g.TH + yl;
       px[m] = (float)x + 0.5f;
       py[m] = (float)y + 0.5f;
-      slot[m] = view - k * g.C;
+      slot[m] = view - k * C;
       ch[m] = u;
       oidx[m] = ((int64_t)y * g.W + x) * 3 + u;
     }
@@ -82,26 +100,62 @@ __global__ void __launch_bounds__(256) k_blend(PanelGeom g, BlendArgs a) {
 #pragma unroll
     for (int m = 0; m < R; ++m) any |= act[m];
     if (!__syncthreads_or(any)) break;
+    // stage one batch: attributes, per-view means and the footprint bits
     const uint32_t e = base + threadIdx.x;
+    uint32_t mask = 0;
     if (e < rg.y) {
       const uint32_t gid = a.list[e];
       const size_t rec = (size_t)k * a.M + gid;
       const float4 co = reinterpret_cast<const float4*>(a.conic_opacity)[rec];
+      const float4 ct = reinterpret_cast<const float4*>(a.color_tau)[rec];
       s_co[threadIdx.x] = make_float4(-0.5f * kLog2e * co.x, -kLog2e * co.y, -0.5f * kLog2e * co.z, co.w);
-      s_col[threadIdx.x] = reinterpret_cast<const float4*>(a.color_tau)[rec];
-      const float2* mp = reinterpret_cast<const float2*>(a.means2d) + rec * g.C;
-      for (int l = 0; l < g.C; ++l) s_mean[threadIdx.x * g.C + l] = mp[l];
+      s_col[threadIdx.x] = ct;
+      const float det = co.x * co.z - co.y * co.y;
+      const float hx = sqrtf(fmaxf(ct.w * co.z / det, 0.f));
+      const float hy = sqrtf(fmaxf(ct.w * co.x / det, 0.f));
+      const float2* mp = reinterpret_cast<const float2*>(a.means2d) + rec * C;
+      for (int l = 0; l < C; ++l) {
+        const float2 mu = mp[l];
+        s_mean[threadIdx.x * C + l] = mu;
+        const bool hit = (mu.x + hx >= bx0) && (mu.x - hx <= bx1) && (mu.y + hy >= by0) &&
+                         (mu.y - hy <= by1);
+        mask |= (uint32_t)hit << l;
+      }
+    }
+    // per-view compaction: s_idx[l][..] lists, in list order, the staged
+    // entries whose view-l region meets the tile
+    for (int l = 0; l < C; ++l) {
+      const unsigned b = __ballot_sync(0xffffffffu, (mask >> l) & 1u);
+      if (lane == 0) s_cnt[l * (NW + 1) + warp] = __popc(b);
+    }
+    __syncthreads();
+    if (threadIdx.x < C) {
+      int run = 0;
+      for (int w = 0; w < NW; ++w) {
+        const int c = s_cnt[threadIdx.x * (NW + 1) + w];
+        s_cnt[threadIdx.x * (NW + 1) + w] = run;
+        run += c;
+      }
+      s_cnt[threadIdx.x * (NW + 1) + NW] = run;
+    }
+    __syncthreads();
+    for (int l = 0; l < C; ++l) {
+      const unsigned b = __ballot_sync(0xffffffffu, (mask >> l) & 1u);
+      if ((mask >> l) & 1u) s_idx[l * NB + s_cnt[l * (NW + 1) + warp] + __popc(b & lt)] = (uint16_t)threadIdx.x;
     }
     __syncthreads();
     const int nbatch = (int)min((uint32_t)NB, rg.y - base);
-    for (int gi = 0; gi < nbatch; ++gi) {
-      const float4 co = s_co[gi];
-      const float4 cl = s_col[gi];
 #pragma unroll
-      for (int m = 0; m < R; ++m) {
-        if (!act[m]) continue;
-        if (COUNT) ++cnt;
-        const float2 mu = s_mean[gi * g.C + slot[m]];
+    for (int m = 0; m < R; ++m) {
+      if (!act[m]) continue;
+      const uint16_t* idx = s_idx + slot[m] * NB;
+      const int cnt = s_cnt[slot[m] * (NW + 1) + NW];
+      int stop = -1;
+      for (int q = 0; q < cnt; ++q) {
+        const int gi = idx[q];
+        if (COUNT) ++n_eval;
+        const float4 co = s_co[gi];
+        const float2 mu = s_mean[gi * C + slot[m]];
         const float dx = px[m] - mu.x;
         const float dy = py[m] - mu.y;
         const float power = co.x * dx * dx + co.z * dy * dy + co.y * dx * dy;
@@ -112,12 +166,16 @@ __global__ void __launch_bounds__(256) k_blend(PanelGeom g, BlendArgs a) {
         const float Tn = T[m] * (1.f - alpha);
         if (Tn < kTMin) {
           act[m] = false;
-          continue;
+          stop = gi;
+          break;
         }
+        const float4 cl = s_col[gi];
         const float c = ch[m] == 0 ? cl.x : (ch[m] == 1 ? cl.y : cl.z);
         acc[m] += c * alpha * T[m];
         T[m] = Tn;
       }
+      // list entries walked in this batch, skipped ones included
+      if (COUNT) n_visit += stop >= 0 ? (unsigned long long)(stop + 1) : (unsigned long long)nbatch;
     }
   }
 #pragma unroll
@@ -127,16 +185,25 @@ __global__ void __launch_bounds__(256) k_blend(PanelGeom g, BlendArgs a) {
     a.out[oidx[m]] = acc[m] + T[m] * bg;
   }
   if (COUNT) {
-    unsigned long long c = cnt;
+    unsigned long long cv = n_visit, ce = n_eval;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(a.eval_counter, c);
+    for (int o = 16; o > 0; o >>= 1) {
+      cv += __shfl_down_sync(0xffffffffu, cv, o);
+      ce += __shfl_down_sync(0xffffffffu, ce, o);
+    }
+    if (lane == 0) {
+      if (cv) atomicAdd(a.eval_counter, cv);
+      if (ce) atomicAdd(a.eval_counter + 1, ce);
+    }
   }
 }
 
 template <int R>
 cudaError_t launch_r(const PanelGeom& g, const BlendArgs& a, int block, cudaStream_t s) {
-  const size_t smem = (size_t)block * (2 * sizeof(float4) + g.C * sizeof(float2));
+  const int nw = block / 32;
+  const size_t smem = (size_t)block * (2 * sizeof(float4) + g.C * sizeof(float2)) +
+                      (((size_t)g.C * block + 1) & ~(size_t)1) * sizeof(uint16_t) +
+                      (size_t)g.C * (nw + 1) * sizeof(int);
   const unsigned grid = (unsigned)((int64_t)g.K * g.T);
   if (a.eval_counter) {
     if (smem > 48 * 1024)

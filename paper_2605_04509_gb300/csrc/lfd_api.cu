@@ -96,7 +96,7 @@ struct lfd_plan {
   // per-frame scratch
   DevBuf proj_means, proj_co, proj_ct, proj_depth;
   DevBuf item_key[2], item_val[2];
-  DevBuf counts, offsets, scan_tmp;
+  DevBuf counts, offsets, scan_tmp, bin_desc;
   DevBuf pair_key[2], pair_val[2];
   DevBuf radix_tmp;
   DevBuf ranges;
@@ -175,7 +175,7 @@ void lfd_plan_destroy(lfd_plan* p) {
   cudaFree(p->seg);
   DevBuf* bufs[] = {&p->proj_means, &p->proj_co,   &p->proj_ct,     &p->proj_depth,
                     &p->item_key[0], &p->item_key[1], &p->item_val[0], &p->item_val[1],
-                    &p->counts,     &p->offsets,   &p->scan_tmp,    &p->pair_key[0],
+                    &p->counts,     &p->offsets,   &p->scan_tmp,    &p->bin_desc,  &p->pair_key[0],
                     &p->pair_key[1], &p->pair_val[0], &p->pair_val[1], &p->radix_tmp,
                     &p->ranges,     &p->small,     &p->host_in[0],  &p->host_in[1],
                     &p->host_in[2], &p->host_in[3], &p->host_in[4], &p->image};
@@ -409,6 +409,7 @@ static int render_projected_impl(lfd_plan* p, int64_t M, const float* means2d,
   if ((rc = p->counts.ensure((size_t)(n_items + 1) * 4)) != LFD_OK) return rc;
   if ((rc = p->offsets.ensure((size_t)(n_items + 1) * 4)) != LFD_OK) return rc;
   if ((rc = p->scan_tmp.ensure(scan_temp_bytes(n_items + 1))) != LFD_OK) return rc;
+  if ((rc = p->bin_desc.ensure((size_t)(n_items + 1) * kBinDescBytes)) != LFD_OK) return rc;
   const uint32_t* order = nullptr;
   if (!key64) {
     // depth-first order: sort the K*M (cluster, depth) items once
@@ -422,11 +423,11 @@ static int render_projected_impl(lfd_plan* p, int64_t M, const float* means2d,
     bool alt = false;
     LFD_CUDA(radix_sort_u64(p->item_key[0].as<uint64_t>(), p->item_key[1].as<uint64_t>(),
                             p->item_val[0].as<uint32_t>(), p->item_val[1].as<uint32_t>(), n_items,
-                            32 + g.bit_k, p->radix_tmp.p, &alt, s));
+                            0, 32 + g.bit_k, p->radix_tmp.p, &alt, s));
     order = p->item_val[alt ? 1 : 0].as<uint32_t>();
   }
   LFD_CUDA(launch_bin_count(g, M, means2d, conic_opacity, color_tau, order, n_items,
-                            p->counts.as<uint32_t>(), s));
+                            p->counts.as<uint32_t>(), p->bin_desc.p, s));
   LFD_CUDA(scan_exclusive(p->counts.as<uint32_t>(), p->offsets.as<uint32_t>(), n_items, p->scan_tmp.p,
                           d_small, s));
   LFD_CUDA(cudaMemcpyAsync(p->h_small, d_small, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
@@ -444,19 +445,21 @@ static int render_projected_impl(lfd_plan* p, int64_t M, const float* means2d,
   LFD_CUDA(launch_bin_emit(g, M, means2d, conic_opacity, color_tau, depth, order, n_items,
                            p->offsets.as<uint32_t>(), key64 ? nullptr : p->pair_key[0].as<uint32_t>(),
                            key64 ? p->pair_key[0].as<uint64_t>() : nullptr,
-                           p->pair_val[0].as<uint32_t>(), s));
+                           p->pair_val[0].as<uint32_t>(), p->bin_desc.p, s));
   if (timing) LFD_CUDA(cudaEventRecord(ev[2], s));
 
-  // ---- stage 3: sort by (tile, cluster[, depth]) ----
+  // ---- stage 3: sort by (tile, cluster, depth) ----
+  // Depth-first mode emits the pairs in (cluster, depth, id) order, so a
+  // stable sort on the tile bits alone yields (tile, cluster, depth, id).
   bool alt = false;
   if (key64)
     LFD_CUDA(radix_sort_u64(p->pair_key[0].as<uint64_t>(), p->pair_key[1].as<uint64_t>(),
                             p->pair_val[0].as<uint32_t>(), p->pair_val[1].as<uint32_t>(), (int64_t)P,
-                            32 + g.bit_k + g.bit_t, p->radix_tmp.p, &alt, s));
+                            0, 32 + g.bit_k + g.bit_t, p->radix_tmp.p, &alt, s));
   else
     LFD_CUDA(radix_sort_u32(p->pair_key[0].as<uint32_t>(), p->pair_key[1].as<uint32_t>(),
                             p->pair_val[0].as<uint32_t>(), p->pair_val[1].as<uint32_t>(), (int64_t)P,
-                            g.bit_k + g.bit_t, p->radix_tmp.p, &alt, s));
+                            g.bit_k, g.bit_k + g.bit_t, p->radix_tmp.p, &alt, s));
   const int kb = alt ? 1 : 0;
   LFD_CUDA(cudaMemsetAsync(p->ranges.p, 0, (size_t)g.T * g.K * sizeof(uint2), s));
   LFD_CUDA(launch_ranges(g, (int64_t)P, key64 ? nullptr : p->pair_key[kb].as<uint32_t>(),
@@ -464,7 +467,7 @@ static int render_projected_impl(lfd_plan* p, int64_t M, const float* means2d,
   if (timing) LFD_CUDA(cudaEventRecord(ev[3], s));
 
   // ---- stage 4: subpixel blend with view-coherent remapping ----
-  if (counting) LFD_CUDA(cudaMemsetAsync(d_small + 1, 0, sizeof(unsigned long long), s));
+  if (counting) LFD_CUDA(cudaMemsetAsync(d_small + 1, 0, 2 * sizeof(unsigned long long), s));
   BlendArgs ba;
   ba.psi = p->psi;
   ba.seg = p->seg;
@@ -495,14 +498,18 @@ static int render_projected_impl(lfd_plan* p, int64_t M, const float* means2d,
   p->last_stream = s;
   if (stats) {
     stats->num_pairs = (int64_t)P;
+    stats->num_visits = -1;
     stats->num_evals = -1;
     stats->ms_project = stats->ms_keygen = stats->ms_sort = stats->ms_blend = -1.f;
     if (counting || timing) {
       if (counting)
-        LFD_CUDA(cudaMemcpyAsync(p->h_small + 1, d_small + 1, sizeof(unsigned long long),
+        LFD_CUDA(cudaMemcpyAsync(p->h_small + 1, d_small + 1, 2 * sizeof(unsigned long long),
                                  cudaMemcpyDeviceToHost, s));
       LFD_CUDA(cudaStreamSynchronize(s));
-      if (counting) stats->num_evals = (int64_t)p->h_small[1];
+      if (counting) {
+        stats->num_visits = (int64_t)p->h_small[1];
+        stats->num_evals = (int64_t)p->h_small[2];
+      }
       if (timing) {
         if (projected_here) LFD_CUDA(cudaEventElapsedTime(&stats->ms_project, ev[0], ev[1]));
         LFD_CUDA(cudaEventElapsedTime(&stats->ms_keygen, ev[1], ev[2]));

@@ -52,18 +52,21 @@ cudaError_t launch_project(const PanelGeom& g, const CamTable& cams, const Proje
 cudaError_t launch_item_keys(const PanelGeom& g, int64_t M, const float* depth,
                              const float* color_tau, uint64_t* keys, uint32_t* vals,
                              cudaStream_t s);
+// Bytes per item of the optional union descriptors the count pass leaves for
+// the emit pass (nullptr: the emit pass recomputes the geometry).
+constexpr size_t kBinDescBytes = 64;
 // tile count of the cluster union per item; items given by `order` (flat
 // k*M + i indices) or natural order when order == nullptr
 cudaError_t launch_bin_count(const PanelGeom& g, int64_t M, const float* means2d,
                              const float* conic_opacity, const float* color_tau,
-                             const uint32_t* order, int64_t n_items, uint32_t* counts,
+                             const uint32_t* order, int64_t n_items, uint32_t* counts, void* desc,
                              cudaStream_t s);
 // emission: key32 = (t << bit_k) | k when keys64 == nullptr, else Eq. 11
 cudaError_t launch_bin_emit(const PanelGeom& g, int64_t M, const float* means2d,
                             const float* conic_opacity, const float* color_tau,
                             const float* depth, const uint32_t* order, int64_t n_items,
                             const uint32_t* offsets, uint32_t* keys32, uint64_t* keys64,
-                            uint32_t* vals, cudaStream_t s);
+                            uint32_t* vals, const void* desc, cudaStream_t s);
 cudaError_t launch_ranges(const PanelGeom& g, int64_t P, const uint32_t* keys32,
                           const uint64_t* keys64, uint2* ranges, cudaStream_t s);
 
@@ -73,13 +76,14 @@ size_t scan_temp_bytes(int64_t n);
 cudaError_t scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, void* temp,
                            unsigned long long* total_dev, cudaStream_t s);
 size_t radix_temp_bytes(int64_t n);
-// stable LSD radix sort of (key, value) over bits [0, bits); ping-pongs
-// between the two buffers; *result_in_alt tells where the result ends up
+// stable LSD radix sort of (key, value) by key bits [begin_bit, end_bit);
+// ping-pongs between the two buffers; *result_in_alt tells where the result
+// ends up
 cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals,
-                           uint32_t* vals_alt, int64_t n, int bits, void* temp,
+                           uint32_t* vals_alt, int64_t n, int begin_bit, int end_bit, void* temp,
                            bool* result_in_alt, cudaStream_t s);
 cudaError_t radix_sort_u64(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals,
-                           uint32_t* vals_alt, int64_t n, int bits, void* temp,
+                           uint32_t* vals_alt, int64_t n, int begin_bit, int end_bit, void* temp,
                            bool* result_in_alt, cudaStream_t s);
 
 // ---- blend (blend.cu) ----
@@ -94,7 +98,7 @@ struct BlendArgs {
   int64_t M;
   float bg[3];
   float* out;
-  unsigned long long* eval_counter;  // non-null: count visited entries
+  unsigned long long* eval_counter;  // non-null: [0] visited entries, [1] evaluated ones
   int max_segment;
 };
 cudaError_t launch_blend(const PanelGeom& g, const BlendArgs& a, cudaStream_t s);

@@ -32,6 +32,15 @@ __device__ __forceinline__ float3 cam_point(const float* c, float x, float y, fl
                      c[6] * x + c[7] * y + c[8] * z + c[11]);
 }
 
+// View-space depth as the bits of the sort key's 32-bit float (Eq. 11):
+// ((R20 mx + R21 my) + R22 mz) + t2, each operation rounded to float in this
+// order. The depth order and the near-plane test are integer decisions taken
+// from this value, so it is evaluated without contraction.
+__device__ __forceinline__ float depth_rn(const float* c, float x, float y, float z) {
+  return __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[6], x), __fmul_rn(c[7], y)), __fmul_rn(c[8], z)),
+                   c[11]);
+}
+
 __global__ void __launch_bounds__(128) k_project(PanelGeom g, CamTable cams, ProjectArgs a) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.M) return;
@@ -72,7 +81,8 @@ __global__ void __launch_bounds__(128) k_project(PanelGeom g, CamTable cams, Pro
   for (int k = 0; k < g.K; ++k) {
     const int jr = min(k * g.C + g.C / 2, g.N - 1);
     const float* cr = cams.c[jr];
-    const float3 p = cam_point(cr, mx, my, mz);
+    float3 p = cam_point(cr, mx, my, mz);
+    p.z = depth_rn(cr, mx, my, mz);
     const size_t ok = (size_t)k * a.M + i;
     float4 co = make_float4(0.f, 0.f, 0.f, o);
     float4 ct = make_float4(0.f, 0.f, 0.f, -1.f);
@@ -154,7 +164,7 @@ __global__ void __launch_bounds__(128) k_project(PanelGeom g, CamTable cams, Pro
       const float* cj = cams.c[j];
       const float3 pj = cam_point(cj, mx, my, mz);
       float2 m2 = make_float2(nanf_, nanf_);
-      if (pj.z > kNear) {
+      if (depth_rn(cj, mx, my, mz) > kNear) {
         const float iz = 1.f / pj.z;
         m2 = make_float2(cj[12] * pj.x * iz + cj[14], cj[13] * pj.y * iz + cj[15]);
       }

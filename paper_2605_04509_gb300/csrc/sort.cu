@@ -121,14 +121,14 @@ __global__ void __launch_bounds__(kScanThreads)
 }
 
 template <typename K>
-__device__ __forceinline__ int digit_of(K key, int shift) {
-  return (int)((key >> shift) & (K)(kRadix - 1));
+__device__ __forceinline__ int digit_of(K key, int shift, int mask) {
+  return (int)((key >> shift) & (K)mask);
 }
 
 template <typename K>
 __global__ void __launch_bounds__(kSortThreads)
-    k_radix_hist(const K* __restrict__ keys, int64_t n, int shift, uint32_t* __restrict__ hist,
-                 int64_t nb) {
+    k_radix_hist(const K* __restrict__ keys, int64_t n, int shift, int mask,
+                 uint32_t* __restrict__ hist, int64_t nb) {
   __shared__ uint32_t s_cnt[kRadix];
   for (int a = threadIdx.x; a < kRadix; a += kSortThreads) s_cnt[a] = 0;
   __syncthreads();
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kSortThreads)
 #pragma unroll 4
   for (int r = 0; r < kSortRounds; ++r) {
     const int64_t idx = base + r * kSortThreads + threadIdx.x;
-    const int d = idx < n ? digit_of(keys[idx], shift) : kRadix;
+    const int d = idx < n ? digit_of(keys[idx], shift, mask) : kRadix;
     const unsigned peers = __match_any_sync(0xffffffffu, d);
     if (d < kRadix && lane == __ffs(peers) - 1) atomicAdd(&s_cnt[d], (uint32_t)__popc(peers));
   }
@@ -146,18 +146,27 @@ __global__ void __launch_bounds__(kSortThreads)
     hist[(int64_t)a * nb + blockIdx.x] = s_cnt[a];
 }
 
+// Stable scatter of one tile. Items are ranked in the tile (warp chunks in
+// order, match-any ranks inside a warp round, warp counters prefixed across
+// warps), placed in shared memory in digit order, and written out so that
+// consecutive threads store consecutive addresses of each digit's run.
 template <typename K>
 __global__ void __launch_bounds__(kSortThreads)
     k_radix_scatter(const K* __restrict__ kin, K* __restrict__ kout, const uint32_t* __restrict__ vin,
-                    uint32_t* __restrict__ vout, int64_t n, int shift,
+                    uint32_t* __restrict__ vout, int64_t n, int shift, int mask,
                     const uint32_t* __restrict__ hist_scanned, int64_t nb) {
+  static_assert(kRadix == kSortThreads, "one digit per thread");
+  extern __shared__ __align__(16) unsigned char s_raw[];
+  K* s_key = reinterpret_cast<K*>(s_raw);
+  uint32_t* s_val = reinterpret_cast<uint32_t*>(s_key + kSortTile);
   __shared__ uint32_t s_wcnt[kSortWarps][kRadix];
   __shared__ uint32_t s_base[kRadix];
+  __shared__ uint32_t s_dstart[kRadix];
+  __shared__ uint32_t s_wsum[kSortWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   for (int a = threadIdx.x; a < kSortWarps * kRadix; a += kSortThreads) (&s_wcnt[0][0])[a] = 0;
-  for (int a = threadIdx.x; a < kRadix; a += kSortThreads)
-    s_base[a] = hist_scanned[(int64_t)a * nb + blockIdx.x];
+  s_base[threadIdx.x] = hist_scanned[(int64_t)threadIdx.x * nb + blockIdx.x];
   __syncthreads();
   // warp w owns the contiguous chunk [base, base + 32 * kSortRounds)
   const int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * 32 * kSortRounds;
@@ -172,7 +181,7 @@ __global__ void __launch_bounds__(kSortThreads)
     if (idx < n) {
       key[r] = kin[idx];
       val[r] = vin[idx];
-      d = digit_of(key[r], shift);
+      d = digit_of(key[r], shift, mask);
     }
     const unsigned peers = __match_any_sync(0xffffffffu, d);
     const int rank = __popc(peers & lt);
@@ -185,7 +194,9 @@ __global__ void __launch_bounds__(kSortThreads)
     dg[r] = d;
   }
   __syncthreads();
-  for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
+  // per digit: exclusive prefix over warps, then the block-wide digit starts
+  {
+    const int d = threadIdx.x;
     uint32_t run = 0;
 #pragma unroll
     for (int w = 0; w < kSortWarps; ++w) {
@@ -193,44 +204,74 @@ __global__ void __launch_bounds__(kSortThreads)
       s_wcnt[w][d] = run;
       run += c;
     }
+    uint32_t x = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_wsum[warp] = x;
+    __syncthreads();
+    uint32_t pre = 0;
+    for (int w = 0; w < warp; ++w) pre += s_wsum[w];
+    s_dstart[d] = pre + x - run;
   }
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
     const int d = dg[r];
     if (d < kRadix) {
-      const uint32_t pos = s_base[d] + s_wcnt[warp][d] + rk[r];
-      kout[pos] = key[r];
-      vout[pos] = val[r];
+      const uint32_t pos = s_dstart[d] + s_wcnt[warp][d] + rk[r];
+      s_key[pos] = key[r];
+      s_val[pos] = val[r];
     }
+  }
+  __syncthreads();
+  const int64_t tile0 = (int64_t)blockIdx.x * kSortTile;
+  const int cnt = (int)min((int64_t)kSortTile, n - tile0);
+  for (int j = threadIdx.x; j < cnt; j += kSortThreads) {
+    const K k = s_key[j];
+    const int d = digit_of(k, shift, mask);
+    const uint32_t out = s_base[d] + ((uint32_t)j - s_dstart[d]);
+    kout[out] = k;
+    vout[out] = s_val[j];
   }
 }
 
 template <typename K>
 cudaError_t radix_sort_impl(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt, int64_t n,
-                            int bits, void* temp, bool* result_in_alt, cudaStream_t s) {
+                            int begin_bit, int end_bit, void* temp, bool* result_in_alt,
+                            cudaStream_t s) {
   *result_in_alt = false;
-  if (n <= 1 || bits <= 0) return cudaSuccess;
+  if (n <= 1 || end_bit <= begin_bit) return cudaSuccess;
   const int64_t nb = (n + kSortTile - 1) / kSortTile;
   uint32_t* hist = reinterpret_cast<uint32_t*>(temp);
   uint32_t* hscan = hist + nb * kRadix;
   void* stemp = hscan + nb * kRadix;
   unsigned long long* total = reinterpret_cast<unsigned long long*>(
       reinterpret_cast<char*>(stemp) + scan_temp_bytes(nb * kRadix));
+  const size_t smem = (size_t)kSortTile * (sizeof(K) + sizeof(uint32_t));
+  {
+    cudaError_t e = cudaFuncSetAttribute(k_radix_scatter<K>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   K* src_k = keys;
   K* dst_k = keys_alt;
   uint32_t* src_v = vals;
   uint32_t* dst_v = vals_alt;
   bool alt = false;
-  for (int shift = 0; shift < bits; shift += kRadixBits) {
-    k_radix_hist<K><<<(unsigned)nb, kSortThreads, 0, s>>>(src_k, n, shift, hist, nb);
+  for (int shift = begin_bit; shift < end_bit; shift += kRadixBits) {
+    const int nbits = end_bit - shift < kRadixBits ? end_bit - shift : kRadixBits;
+    const int mask = (1 << nbits) - 1;
+    k_radix_hist<K><<<(unsigned)nb, kSortThreads, 0, s>>>(src_k, n, shift, mask, hist, nb);
     note_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = scan_exclusive(hist, hscan, nb * kRadix, stemp, total, s);
     if (e != cudaSuccess) return e;
-    k_radix_scatter<K><<<(unsigned)nb, kSortThreads, 0, s>>>(src_k, dst_k, src_v, dst_v, n, shift,
-                                                             hscan, nb);
+    k_radix_scatter<K><<<(unsigned)nb, kSortThreads, smem, s>>>(src_k, dst_k, src_v, dst_v, n,
+                                                                shift, mask, hscan, nb);
     note_launches(1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -274,17 +315,17 @@ size_t radix_temp_bytes(int64_t n) {
 }
 
 cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals,
-                           uint32_t* vals_alt, int64_t n, int bits, void* temp,
+                           uint32_t* vals_alt, int64_t n, int begin_bit, int end_bit, void* temp,
                            bool* result_in_alt, cudaStream_t s) {
-  return radix_sort_impl<uint32_t>(keys, keys_alt, vals, vals_alt, n, bits, temp, result_in_alt,
-                                   s);
+  return radix_sort_impl<uint32_t>(keys, keys_alt, vals, vals_alt, n, begin_bit, end_bit, temp,
+                                   result_in_alt, s);
 }
 
 cudaError_t radix_sort_u64(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals,
-                           uint32_t* vals_alt, int64_t n, int bits, void* temp,
+                           uint32_t* vals_alt, int64_t n, int begin_bit, int end_bit, void* temp,
                            bool* result_in_alt, cudaStream_t s) {
-  return radix_sort_impl<uint64_t>(keys, keys_alt, vals, vals_alt, n, bits, temp, result_in_alt,
-                                   s);
+  return radix_sort_impl<uint64_t>(keys, keys_alt, vals, vals_alt, n, begin_bit, end_bit, temp,
+                                   result_in_alt, s);
 }
 
 }  // namespace lfd

@@ -61,7 +61,7 @@ class CPlanInfo(ct.Structure):
 
 
 class CStats(ct.Structure):
-    _fields_ = [("num_pairs", ct.c_int64), ("num_evals", ct.c_int64),
+    _fields_ = [("num_pairs", ct.c_int64), ("num_visits", ct.c_int64), ("num_evals", ct.c_int64),
                 ("ms_project", ct.c_float), ("ms_keygen", ct.c_float),
                 ("ms_sort", ct.c_float), ("ms_blend", ct.c_float)]
 

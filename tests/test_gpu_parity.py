@@ -11,7 +11,7 @@ import pytest
 import oracle
 from paper_2605_04509_gb300 import synth
 
-from .helpers import assert_image_close, image_metrics
+from .helpers import assert_image_close, assert_render_matches, image_metrics
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -113,7 +113,8 @@ def test_projection_matches_fp64(tiny, c):
     gc, rc = got["conic_opacity"][valid][:, :3], ref["conic_opacity"][valid][:, :3]
     scale = np.abs(rc).max(axis=1, keepdims=True)
     assert (np.abs(gc - rc) <= 1e-4 * scale + 1e-7).all()
-    np.testing.assert_allclose(got["depth"][valid], ref["depth"][valid], rtol=1e-6)
+    # the depth (sort-key precision, Eq. 11) is one fixed FP32 sequence on both sides
+    np.testing.assert_array_equal(got["depth"][valid], ref["depth"][valid])
     np.testing.assert_allclose(got["color_tau"][valid][:, :3], ref["color_tau"][valid][:, :3],
                                atol=2e-5)
     np.testing.assert_allclose(got["color_tau"][valid][:, 3], ref["color_tau"][valid][:, 3],
@@ -186,10 +187,16 @@ def test_blend_matches_oracle_on_same_lists(tiny, c):
     p64 = oracle_proj_from_f32(attrs, w.panel.num_views, c)
     V = oracle.view_index(w.panel)
     want, n_eval = oracle.blend_lists(p64, V, c, ref["ranges"], ref["list"])
-    m = assert_image_close(img.cpu().numpy(), want, f"blend C={c}")
+    with oracle.alpha_min(oracle.ALPHA_MIN * (1 - 1e-3)):
+        lo, _ = oracle.blend_lists(p64, V, c, ref["ranges"], ref["list"])
+    with oracle.alpha_min(oracle.ALPHA_MIN * (1 + 1e-3)):
+        hi, _ = oracle.blend_lists(p64, V, c, ref["ranges"], ref["list"])
+    m = assert_render_matches(img.cpu().numpy(), want, lo, hi, f"blend C={c}")
     assert m["psnr"] > 60
-    # the GPU's count of visited list entries agrees with the oracle's walk
-    assert abs(st["num_evals"] - n_eval) <= 1e-3 * n_eval
+    # the GPU's count of visited list entries agrees with the oracle's walk;
+    # the per-view footprint test evaluates only a subset of them
+    assert abs(st["num_visits"] - n_eval) <= 1e-3 * n_eval
+    assert 0 < st["num_evals"] <= st["num_visits"]
     plan.close()
 
 
@@ -201,8 +208,8 @@ def test_render_matches_fp64_oracle(tiny, c, sort_mode):
     img, st = plan.render(lfd.scene_to_device(scene), cams)
     proj = oracle.project(scene, cams, w.panel.width, w.panel.height, c)
     V = oracle.view_index(w.panel)
-    ref, _ = oracle.render(proj, V, c, mode=1)
-    m = assert_image_close(img.cpu().numpy(), ref, f"render C={c}")
+    ref, lo, hi = oracle.render_bracket(proj, V, c, mode=1)
+    m = assert_render_matches(img.cpu().numpy(), ref, lo, hi, f"render C={c}")
     assert m["psnr"] > 60 and st["num_pairs"] > 0
     plan.close()
 
@@ -216,8 +223,8 @@ def test_render_ragged_panel(tile):
     plan = lfd.Plan(panel, tile=tile, views_per_cluster=4)
     img, _ = plan.render(lfd.scene_to_device(scene), cams)
     proj = oracle.project(scene, cams, panel.width, panel.height, 4)
-    ref, _ = oracle.render(proj, oracle.view_index(panel), 4, mode=1)
-    assert_image_close(img.cpu().numpy(), ref, f"ragged {tile}")
+    ref, lo, hi = oracle.render_bracket(proj, oracle.view_index(panel), 4, mode=1, tile=tile)
+    assert_render_matches(img.cpu().numpy(), ref, lo, hi, f"ragged {tile}")
     plan.close()
 
 
@@ -246,8 +253,8 @@ def test_edge_cases(tiny):
         plan = lfd.Plan(panel, views_per_cluster=c)
         img, _ = plan.render(lfd.scene_to_device(sc), cm)
         proj = oracle.project(sc, cm, panel.width, panel.height, c)
-        ref, _ = oracle.render(proj, oracle.view_index(panel), c, mode=1)
-        assert_image_close(img.cpu().numpy(), ref, f"N={nv} C={c}")
+        ref, lo, hi = oracle.render_bracket(proj, oracle.view_index(panel), c, mode=1)
+        assert_render_matches(img.cpu().numpy(), ref, lo, hi, f"N={nv} C={c}")
         plan.close()
 
 
@@ -307,13 +314,12 @@ def test_paper4k_sampled_crops():
     dens = np.clip(got, 0, 1).sum(-1)
     yy, xx = np.unravel_index(np.argmax(dens), dens.shape)
     rng = np.random.default_rng(8)
-    crops = [(min(xx // 16, 239) * 16, min(yy // 16, 134) * 16), (1920, 1072), (3824, 2144)]
-    crops += [(int(rng.integers(0, 240)) * 16, int(rng.integers(0, 135)) * 16) for _ in range(3)]
-    worst = None
-    for x0, y0 in crops:
-        crop = (x0, y0, x0 + 16, y0 + 16)
-        ref, _ = oracle.render(proj, V, c, crop=crop, mode=1)
-        m = image_metrics(got[y0:y0 + 16, x0:x0 + 16], ref)
-        worst = m if worst is None or m["max_err"] > worst["max_err"] else worst
-        assert_image_close(got[y0:y0 + 16, x0:x0 + 16], ref, f"crop {crop}")
+    crops = [(min(xx // 16, 239) * 16, min(yy // 16, 134) * 16, 16, 16), (3824, 2144, 16, 16),
+             (1664, 952, 512, 256)]  # the central 512x256 crop holds the densest blobs
+    crops += [(int(rng.integers(0, 240)) * 16, int(rng.integers(0, 135)) * 16, 16, 16)
+              for _ in range(3)]
+    for x0, y0, cw, ch in crops:
+        crop = (x0, y0, x0 + cw, y0 + ch)
+        ref, lo, hi = oracle.render_bracket(proj, V, c, crop=crop, mode=1)
+        assert_render_matches(got[y0:y0 + ch, x0:x0 + cw], ref, lo, hi, f"crop {crop}")
     plan.close()

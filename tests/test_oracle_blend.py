@@ -211,3 +211,18 @@ def test_background_and_empty_scene():
     img, n = oracle.render(proj, V, 1, mode=0, bg=(0.25, 0.5, 1.0))
     assert n == 0
     np.testing.assert_array_equal(img, np.broadcast_to([0.25, 0.5, 1.0], (H, W, 3)))
+
+
+def test_alpha_threshold_parameter():
+    # One Gaussian with peak opacity o: raising the skip threshold above o
+    # removes it everywhere; the default threshold is restored afterwards.
+    W, H = 16, 16
+    V = oracle.view_index(synth.Panel(W, H, 1, 0.0, 5.0, 0.0))
+    scene = _scene([[0, 0, 2.0]], [[0.05] * 3], [0.5], [(0.9, 0.9, 0.9)])
+    proj = oracle.project(scene, _cams([0.0], 200.0, 8.5, 8.5), W, H, 1)
+    base, _ = oracle.render(proj, V, 1, mode=0)
+    with oracle.alpha_min(0.51):
+        gone, _ = oracle.render(proj, V, 1, mode=0)
+    again, _ = oracle.render(proj, V, 1, mode=0)
+    assert base.max() > 0.3 and gone.max() == 0.0
+    np.testing.assert_array_equal(base, again)
