@@ -205,6 +205,31 @@ LFD_API int lfd_render_host(lfd_plan *plan, const lfd_gaussians *g_host,
 LFD_API int lfd_plan_copy_lists(const lfd_plan *plan, uint32_t *list, uint32_t *ranges,
                         uint64_t *keys, int64_t capacity);
 
+/* Allocation-free variant of lfd_render_projected, for callers that must
+ * not allocate device memory while they render: code that runs while a
+ * stream is being captured into a CUDA graph (allocation calls cannot be
+ * captured), real-time loops that cannot afford the device-wide
+ * synchronisation cudaMalloc and cudaFree imply, and hosts whose own memory
+ * manager owns the device heap. The paper has no counterpart.
+ * Same arguments, stages and results (bit for bit) as lfd_render_projected;
+ * the plan must have been created beforehand. All scratch memory comes from
+ * one fixed array of about 4.4 MB inside the library (every GPU that loads
+ * the library holds it until the process exits), which bounds the frame:
+ * K * M <= 32768 projected items, T * K <= 16384 (tile, cluster) lists and
+ * P <= 131072 Gaussian-tile pairs; larger frames return LFD_ERR_CAPACITY
+ * with a message saying which limit, and the output is left untouched when
+ * the item or list limit is hit. The call allocates nothing, neither on the
+ * device nor on the host; like lfd_render_projected it reads the pair count
+ * back (one stream synchronisation). The first call on a device looks up
+ * the array's device address once (set-up); make that first call before any
+ * stream capture. Every call shares the one array and leaves its contents
+ * behind, so calls that overlap on the GPU (other streams, other host
+ * threads) race: serialise them. stats may be NULL; only num_pairs is filled. */
+LFD_API int lfd_render_projected_noalloc(lfd_plan *plan, int64_t M, const float *means2d,
+                                         const float *conic_opacity, const float *color_tau,
+                                         const float *depth, float *out_rgb, void *stream,
+                                         lfd_stats *stats);
+
 /* Stage times accumulated over frames rendered with LFD_FLAG_STAGE_TIMING,
  * measured with CUDA events on each frame's stream and folded in without
  * extra synchronisation (a frame's events are read at the next frame's

@@ -140,6 +140,28 @@ int fold_stage_times(lfd_plan* p, int set) {
 
 }  // namespace
 
+namespace lfd {
+
+int plan_view(const lfd_plan* p, PlanView* out) {
+  if (!p || !out) return LFD_ERR_INVALID;
+  out->g = p->g;
+  out->psi = p->psi;
+  out->seg = p->seg;
+  out->max_segment = p->max_segment;
+  out->sort_mode = p->opts.sort_mode;
+  out->bg[0] = p->opts.bg[0];
+  out->bg[1] = p->opts.bg[1];
+  out->bg[2] = p->opts.bg[2];
+  out->h_small = p->h_small;
+  return LFD_OK;
+}
+
+int set_error(int code, const char* msg) { return fail(code, msg); }
+
+int set_cuda_error(cudaError_t e, const char* where) { return fail_cuda(e, where); }
+
+}  // namespace lfd
+
 extern "C" {
 
 int lfd_version(void) { return 100; }

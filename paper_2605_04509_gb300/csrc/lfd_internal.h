@@ -103,4 +103,18 @@ struct BlendArgs {
 };
 cudaError_t launch_blend(const PanelGeom& g, const BlendArgs& a, cudaStream_t s);
 
+// ---- read-only view of a plan and error reporting (lfd_api.cu) ----
+struct PlanView {
+  PanelGeom g;
+  const uint32_t* psi;
+  const int32_t* seg;
+  int max_segment;
+  int sort_mode;
+  float bg[3];
+  unsigned long long* h_small;  // pinned host words owned by the plan
+};
+int plan_view(const lfd_plan* p, PlanView* out);
+int set_error(int code, const char* msg);
+int set_cuda_error(cudaError_t e, const char* where);
+
 }  // namespace lfd

@@ -98,6 +98,8 @@ def load() -> ct.CDLL:
                                       ct.POINTER(CStats)], ct.c_int),
             "lfd_render": ([_P, ct.POINTER(CGaussians), ct.POINTER(CCamera), ct.c_int32, _P, _P,
                             ct.POINTER(CStats)], ct.c_int),
+            "lfd_render_projected_noalloc": ([_P, ct.c_int64, _P, _P, _P, _P, _P, _P,
+                                              ct.POINTER(CStats)], ct.c_int),
             "lfd_render_host": ([_P, ct.POINTER(CGaussians), ct.POINTER(CCamera), ct.c_int32,
                                  _P, _P, ct.POINTER(CStats)], ct.c_int),
             "lfd_plan_copy_lists": ([_P, _P, _P, _P, ct.c_int64], ct.c_int),
@@ -243,6 +245,18 @@ class Plan:
         out = self._image(out)
         st = CStats()
         _check(load().lfd_render_projected(
+            self._h, M, _dptr(attrs["means2d"]), _dptr(attrs["conic_opacity"]),
+            _dptr(attrs["color_tau"]), _dptr(attrs["depth"]), _dptr(out),
+            _stream_ptr(stream), ct.byref(st)))
+        return out, st.as_dict()
+
+    def render_projected_noalloc(self, attrs, out=None, stream=None) -> Tuple[object, Dict]:
+        """lfd_render_projected_noalloc: the same stages with the library's
+        fixed scratch array (small frames only; no device allocation)."""
+        M = int(attrs["depth"].shape[1])
+        out = self._image(out)
+        st = CStats()
+        _check(load().lfd_render_projected_noalloc(
             self._h, M, _dptr(attrs["means2d"]), _dptr(attrs["conic_opacity"]),
             _dptr(attrs["color_tau"]), _dptr(attrs["depth"]), _dptr(out),
             _stream_ptr(stream), ct.byref(st)))
