@@ -59,6 +59,7 @@ def parse_args():
     ap.add_argument("--tile", default="16x16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fullframe", action="store_true", help="skip the full-frame baseline")
     ap.add_argument("--cpu-crop", default="1024x512", help="WxH of the oracle's central crop")
     return ap.parse_args()
 
@@ -171,6 +172,23 @@ def gpu_id_for(torch, index: int) -> str:
 # ---------------------------------------------------------------------------
 # CPU oracle runs (bounded samples)
 # ---------------------------------------------------------------------------
+
+def blend_traffic_bytes():
+    """DRAM bytes (read + write) of one blend launch on this workload, from the
+    ncu capture summarised in profiles/k_blend_traffic.txt, or None when the
+    blend source has changed since that capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_blend_traffic.txt")
+    src = os.path.join(ROOT, "paper_2605_04509_gb300", "csrc", "blend.cu")
+    try:
+        fields = dict(line.split(":", 1) for line in open(path) if ":" in line)
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if fields.get("blend_cu_sha256", "").strip() != digest:
+            return None
+        return int(fields["dram_bytes_per_launch"].strip())
+    except (OSError, KeyError, ValueError):
+        return None
+
 
 def central_crop(panel, cw, ch):
     cw, ch = min(cw, panel.width), min(ch, panel.height)
@@ -302,8 +320,10 @@ def run_ours(args):
     achieved = E * OPS_PER_EVAL / (blend_ms * 1e-3) / 1e12
     peak = SMS * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12
     ex2_frac = E / (blend_ms * 1e-3) / (SMS * MUFU_LANES * SM_MAX_MHZ * 1e6)
+    traffic = blend_traffic_bytes() if (args.workload == "paper4k" and not args.gaussians
+                                        and C == 8 and args.tile == "16x16") else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "k_blend",
+                "frac": achieved / peak, "traffic": traffic, "kernel": "k_blend",
                 "units": f"E = {E} visited (subpixel, Gaussian) evaluations per launch x "
                          f"{OPS_PER_EVAL} FP32 ops; peak = 152 SMs x 128 FP32 lanes x 2070 MHz "
                          f"(of fallback unit counts; the measured peaks file has no FP32 figure)",
@@ -324,6 +344,28 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+
+    if not args.no_fullframe:
+        # the paper's full-frame baseline on the same box: every view rendered
+        # whole (one view per cluster), then interlaced
+        ff_out = torch.empty_like(out)
+        for _ in range(2):
+            plan.render_fullframe(dscene, cams, ff_out, stream)
+        n_ff = 3
+        barrier(world, device)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(n_ff):
+            plan.render_fullframe(dscene, cams, ff_out, stream)
+        f1.record(stream)
+        torch.cuda.synchronize(device)
+        ff_ms = max_over_ranks(f0.elapsed_time(f1) / n_ff, world, device)
+        line["fullframe_baseline"] = {
+            "value": world / (ff_ms / 1000.0), "unit": "frames/s", "ms_per_frame": ff_ms,
+            "frames": n_ff, "speedup_of_subpixel_path": (ff_ms / (ms / args.steps)),
+            "what": "all 45 views rendered as full 3840x2160 3DGS images (per-view lists, one alpha "
+                    "per pixel), interlaced in the same kernel"}
 
     if not args.no_e2e:
         # end to end through the host-buffer entry point: pinned Gaussians in,

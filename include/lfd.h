@@ -25,10 +25,10 @@
  *    calling thread's last failure.
  *
  * Layouts (row-major, float32 unless stated)
- *  - Gaussians (Sec. 3.3): means [M][3]; scales [M][3] (activated, > 0);
- *    quats [M][4] in (w, x, y, z) order (normalised inside); opacities [M]
- *    (activated, in [0, 1]); sh [M][(d+1)^2][3] real SH coefficients of
- *    degree d <= 3 in the 3DGS basis.
+ *  - Gaussians (Sec. 3.3): means [M][3] (FP32); scales [M][3] (activated,
+ *    > 0); quats [M][4] in (w, x, y, z) order (normalised inside); opacities
+ *    [M] (activated, in [0, 1]); sh [M][(d+1)^2][3] real SH coefficients of
+ *    degree d <= 3 in the 3DGS basis; the last four in FP32, FP16 or BF16.
  *  - Camera: world->camera rotation R (row-major 3x3), translation t,
  *    pinhole fx, fy, cx, cy in pixels (x right, y down, z forward). Every
  *    view renders at panel resolution.
@@ -100,8 +100,10 @@ typedef struct {
 } lfd_panel;
 
 /* Rendering options. tile_w * tile_h <= 512, both in [4, 64]; C in
- * [1, 32]; remap must be 1 (view-coherent remap, Sec. 4.3); sort_mode one of
- * LFD_SORT_*; bg is the background colour added as T * bg. */
+ * [1, 32] (C = 1: no attribute reuse); remap 1 = view-coherent remapping
+ * (Sec. 4.3), 0 = subpixels in raster order, each thread walking its own list
+ * (the ablation "w/o remap"; same image); sort_mode one of LFD_SORT_*; bg is
+ * the background colour added as T * bg. */
 typedef struct {
   int32_t tile_w, tile_h;
   int32_t views_per_cluster;
@@ -110,10 +112,19 @@ typedef struct {
   float bg[3];
 } lfd_opts;
 
+/* Storage type of the Gaussians' scales, rotations, opacities and SH
+ * coefficients (means are always FP32). Everything after the load - the
+ * 2D-covariance inverse, the blend and the transmittance product - is FP32. */
+#define LFD_DTYPE_F32 0
+#define LFD_DTYPE_F16 1
+#define LFD_DTYPE_BF16 2
+
 typedef struct {
-  const float *means, *scales, *quats, *opacities, *sh; /* device */
+  const float *means;                          /* device, FP32 [M][3] */
+  const void *scales, *quats, *opacities, *sh; /* device, attr_dtype */
   int64_t count;
   int32_t sh_degree;
+  int32_t attr_dtype;                          /* LFD_DTYPE_* (0 = FP32) */
 } lfd_gaussians;
 
 typedef struct {
@@ -187,6 +198,37 @@ LFD_API int lfd_render_projected(lfd_plan *plan, int64_t M, const float *means2d
  * lfd_render_projected. */
 LFD_API int lfd_render(lfd_plan *plan, const lfd_gaussians *g, const lfd_camera *cams,
                int32_t num_cams, float *out_rgb, void *stream, lfd_stats *stats);
+
+/* Backward of lfd_render (not in the paper): given dL/dI for the image of
+ * the plan's last lfd_render frame (grad_rgb, device [H][W][3]) and the same
+ * Gaussians and cameras, writes dL/d(means, scales, quats, opacities, sh)
+ * into caller-owned FP32 device arrays shaped like the inputs (overwritten).
+ * The blend gradient is taken through Eq. 9-10 with the 3DGS rules; each
+ * subpixel re-blends its list to find its final transmittance and where it
+ * stopped (no per-subpixel state is kept by the forward), then walks back to
+ * front. The projection gradient follows Eq. 5-6: every view's 2D mean, and
+ * the representative view's covariance (with the Jacobian's dependence on the
+ * mean and the 1.3 tan(fov/2) clamp), conic inverse and SH colour (including
+ * its view direction). Needs FP32 attributes and the remapped blend;
+ * LFD_ERR_STATE if the last frame was not an
+ * lfd_render of this Gaussian count. Asynchronous on stream. */
+LFD_API int lfd_render_backward(lfd_plan *plan, const lfd_gaussians *g, const lfd_camera *cams,
+                                int32_t num_cams, const float *grad_rgb, float *grad_means,
+                                float *grad_scales, float *grad_quats, float *grad_opacities,
+                                float *grad_sh, void *stream);
+
+/* The full-frame baseline the paper compares against (Sec. 1, Sec. 5.1; the
+ * "3DGS" rows of T1/T2): every one of the N views rendered as a whole W x H
+ * 3DGS image with its own projection (no attribute reuse: one view per
+ * cluster) and its own per-tile lists, one alpha per pixel for all three
+ * channels, then each subpixel (x, y, u) taken from the image of its view
+ * V[x, y, u] (fused into the write). Same arguments and output as
+ * lfd_render; the plan's tile shape, sort mode and background apply. The
+ * first call builds a one-view-per-cluster companion plan owned by this plan.
+ * Renders the same image as lfd_render with views_per_cluster = 1 (up to
+ * FP32 rounding) at N x 8/3 the blend work. */
+LFD_API int lfd_render_fullframe(lfd_plan *plan, const lfd_gaussians *g, const lfd_camera *cams,
+                                 int32_t num_cams, float *out_rgb, void *stream, lfd_stats *stats);
 
 /* End-to-end variant for callers holding HOST buffers: the Gaussians in g
  * and out_rgb are host pointers (pinned memory gives the fastest copies). The

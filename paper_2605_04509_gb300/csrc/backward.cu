@@ -1,0 +1,437 @@
+// Backward pass of the interlaced render: gradients of a loss of the image
+// with respect to the Gaussians' means, scales, rotations, opacities and SH
+// coefficients. Not in the paper; it differentiates the same definitions
+// (Eq. 5-6 projection with attribute reuse, Eq. 9-10 blend with the 3DGS
+// rules). No per-subpixel lists are stored by the forward pass: each subpixel
+// re-blends its (tile, cluster) list front to back to find its final
+// transmittance and the entry where it stopped, then walks back to front.
+#include "lfd_internal.h"
+
+namespace lfd {
+namespace {
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTMin = 1e-4f;
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// ---------------------------------------------------------------------------
+// blend backward: one CTA per (tile, cluster) run of Psi, one subpixel per
+// thread; the list is staged in shared memory batch by batch, first front to
+// back (forward replay), then from the last needed batch back to the first.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_blend_backward(PanelGeom g, BlendArgs a, BlendGrads gr) {
+  extern __shared__ float4 smem[];
+  const int NB = blockDim.x;
+  const int C = g.C;
+  float4* s_co = smem;                                        // raw conic (a, b, c), opacity
+  float4* s_col = smem + NB;                                  // colour
+  float2* s_mean = reinterpret_cast<float2*>(smem + 2 * NB);  // [C][NB]
+  uint32_t* s_gid = reinterpret_cast<uint32_t*>(s_mean + C * NB);
+  const int k = blockIdx.x / g.T;
+  const int t = blockIdx.x - k * g.T;
+  const int s0 = a.seg[(size_t)t * (g.K + 1) + k];
+  const int n = a.seg[(size_t)t * (g.K + 1) + k + 1] - s0;
+  if (n <= 0) return;
+  const uint2 rg = a.ranges[(size_t)t * g.K + k];
+  if (rg.x == rg.y) return;
+  const int tx = t % g.TX, ty = t / g.TX;
+  const int lane = threadIdx.x & 31;
+  __shared__ uint32_t s_last;
+  // runs longer than the block are processed in chunks of blockDim subpixels
+  for (int chunk = 0; chunk < n; chunk += NB) {
+  const int r = chunk + threadIdx.x;
+  bool act = r < n;
+  float px = 0.f, py = 0.f, G = 0.f;
+  int slot = 0, ch = 0;
+  if (act) {
+    const uint32_t e = a.psi[(size_t)t * g.cap + s0 + r];
+    const int view = (int)(e >> 16);
+    const int loc = (int)(e & 0xffffu);
+    const int xl = (loc / 3) % g.TW, yl = (loc / 3) / g.TW;
+    const int x = tx * g.TW + xl, y = ty * g.TH + yl;
+    ch = loc % 3;
+    px = (float)x + 0.5f;
+    py = (float)y + 0.5f;
+    slot = view - k * C;
+    G = gr.grad_out[((int64_t)y * g.W + x) * 3 + ch];
+  }
+  const bool live = act;
+
+  auto stage = [&](uint32_t base) {
+    const uint32_t e = base + threadIdx.x;
+    if (e < rg.y) {
+      const uint32_t gid = a.list[e];
+      const size_t rec = (size_t)k * a.M + gid;
+      s_co[threadIdx.x] = reinterpret_cast<const float4*>(a.conic_opacity)[rec];
+      s_col[threadIdx.x] = reinterpret_cast<const float4*>(a.color_tau)[rec];
+      const float2* mp = reinterpret_cast<const float2*>(a.means2d) + rec * C;
+      for (int l = 0; l < C; ++l) s_mean[l * NB + threadIdx.x] = mp[l];
+      s_gid[threadIdx.x] = gid;
+    }
+  };
+  // the opacity of an entry for this subpixel, exactly as the forward blend
+  // computes it (0 when skipped); also returns e^power and whether clamped
+  auto opacity_of = [&](int gi, float& vexp, bool& clamped) -> float {
+    const float4 co = s_co[gi];
+    const float2 mu = s_mean[slot * NB + gi];
+    const float dx = px - mu.x, dy = py - mu.y;
+    const float power = (-0.5f * kLog2e * co.x) * dx * dx + (-0.5f * kLog2e * co.z) * dy * dy +
+                        (-kLog2e * co.y) * dx * dy;
+    if (power > 0.f) return 0.f;
+    const float v = co.w * ex2_approx(power);
+    if (!(v >= kAlphaMin)) return 0.f;
+    vexp = v / co.w;
+    clamped = v > kAlphaMax;
+    return fminf(kAlphaMax, v);
+  };
+
+  // forward replay: final transmittance and the first entry not added
+  float T = 1.f;
+  uint32_t stop = rg.y;  // global list index where this subpixel stopped
+  for (uint32_t base = rg.x; base < rg.y; base += (uint32_t)NB) {
+    if (!__syncthreads_or(act)) break;
+    stage(base);
+    __syncthreads();
+    if (!act) continue;
+    const int nbatch = (int)min((uint32_t)NB, rg.y - base);
+    for (int gi = 0; gi < nbatch; ++gi) {
+      float ve;
+      bool cl;
+      const float alpha = opacity_of(gi, ve, cl);
+      if (alpha == 0.f) continue;
+      const float Tn = T * (1.f - alpha);
+      if (Tn < kTMin) {
+        act = false;
+        stop = base + (uint32_t)gi;
+        break;
+      }
+      T = Tn;
+    }
+  }
+  // back to front over [rg.x, stop): R is the colour of everything behind
+  const float bgc = ch == 0 ? a.bg[0] : (ch == 1 ? a.bg[1] : a.bg[2]);
+  float R = bgc;
+  uint32_t last = live ? stop : rg.x;
+  // the block's furthest stop
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = rg.x;
+  __syncthreads();
+  if (live) atomicMax(&s_last, last);
+  __syncthreads();
+  const uint32_t end = s_last;
+  if (end == rg.x) continue;
+  const uint32_t nb_total = (end - rg.x + NB - 1) / NB;
+  for (int b = (int)nb_total - 1; b >= 0; --b) {
+    const uint32_t base = rg.x + (uint32_t)b * NB;
+    __syncthreads();
+    stage(base);
+    __syncthreads();
+    const int nbatch = (int)min((uint32_t)NB, end - base);
+    for (int gi = nbatch - 1; gi >= 0; --gi) {
+      float d_mx = 0.f, d_my = 0.f, d_a = 0.f, d_b = 0.f, d_c = 0.f, d_o = 0.f, d_col = 0.f;
+      bool any = false;
+      if (live && base + (uint32_t)gi < last) {
+        float ve = 0.f;
+        bool cl = false;
+        const float alpha = opacity_of(gi, ve, cl);
+        if (alpha > 0.f) {
+          any = true;
+          const float4 col4 = s_col[gi];
+          const float c = ch == 0 ? col4.x : (ch == 1 ? col4.y : col4.z);
+          const float Ti = T / (1.f - alpha);  // transmittance in front of this entry
+          d_col = alpha * Ti * G;
+          const float dalpha = (c - R) * Ti * G;
+          R = c * alpha + (1.f - alpha) * R;
+          T = Ti;
+          if (!cl) {
+            const float4 co = s_co[gi];
+            const float2 mu = s_mean[slot * NB + gi];
+            const float dx = px - mu.x, dy = py - mu.y;
+            const float dpower = dalpha * alpha;  // d alpha / d power = alpha
+            d_o = dalpha * ve;
+            // power = -(a dx^2 + 2 b dx dy + c dy^2) / 2, dx = px - mu_x
+            d_mx = dpower * (co.x * dx + co.y * dy);
+            d_my = dpower * (co.y * dx + co.z * dy);
+            d_a = -0.5f * dpower * dx * dx;
+            d_b = -dpower * dx * dy;
+            d_c = -0.5f * dpower * dy * dy;
+          }
+        }
+      }
+      // conic and opacity are shared by the warp's lanes: reduce first
+      const unsigned want = __ballot_sync(0xffffffffu, any);
+      if (!want) continue;
+      float ra = d_a, rb = d_b, rc = d_c, ro = d_o;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        ra += __shfl_xor_sync(0xffffffffu, ra, off);
+        rb += __shfl_xor_sync(0xffffffffu, rb, off);
+        rc += __shfl_xor_sync(0xffffffffu, rc, off);
+        ro += __shfl_xor_sync(0xffffffffu, ro, off);
+      }
+      const uint32_t gid = s_gid[gi];
+      const size_t rec = (size_t)k * a.M + gid;
+      if (lane == __ffs(want) - 1) {
+        atomicAdd(&gr.grad_conic[4 * rec + 0], ra);
+        atomicAdd(&gr.grad_conic[4 * rec + 1], rb);
+        atomicAdd(&gr.grad_conic[4 * rec + 2], rc);
+        atomicAdd(&gr.grad_opac[gid], ro);
+      }
+      if (any) {
+        atomicAdd(&gr.grad_color[4 * rec + ch], d_col);
+        float* gm = gr.grad_means2d + 2 * (rec * C + slot);
+        atomicAdd(gm, d_mx);
+        atomicAdd(gm + 1, d_my);
+      }
+    }
+  }
+  }  // chunk
+}
+
+// ---------------------------------------------------------------------------
+// projection backward: one thread per Gaussian, every cluster and slot
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float3 cam_point(const float* c, float x, float y, float z) {
+  return make_float3(c[0] * x + c[1] * y + c[2] * z + c[9], c[3] * x + c[4] * y + c[5] * z + c[10],
+                     c[6] * x + c[7] * y + c[8] * z + c[11]);
+}
+
+constexpr float kC0 = 0.28209479177387814f;
+constexpr float kC1 = 0.4886025119029199f;
+constexpr float kC2a = 1.0925484305920792f;
+constexpr float kC2b = 0.31539156525252005f;
+constexpr float kC2c = 0.5462742152960396f;
+constexpr float kC3a = 0.5900435899266435f;
+constexpr float kC3b = 2.890611442640554f;
+constexpr float kC3c = 0.4570457994644658f;
+constexpr float kC3d = 0.3731763325901154f;
+constexpr float kC3e = 1.445305721320277f;
+
+__global__ void __launch_bounds__(128) k_project_backward(PanelGeom g, CamTable cams, ProjectArgs a,
+                                                          BlendGrads gr, ParamGrads out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.M) return;
+  const float* means = a.means;
+  const float* scales = reinterpret_cast<const float*>(a.scales);
+  const float* quats = reinterpret_cast<const float*>(a.quats);
+  const float* opac = reinterpret_cast<const float*>(a.opac);
+  const float* shs = reinterpret_cast<const float*>(a.sh);
+  const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
+  const float qr[4] = {quats[4 * i], quats[4 * i + 1], quats[4 * i + 2], quats[4 * i + 3]};
+  const float sx = scales[3 * i], sy = scales[3 * i + 1], sz = scales[3 * i + 2];
+  const float o = opac[i];
+  const int ncoef = (a.sh_degree + 1) * (a.sh_degree + 1);
+
+  const float qn = rsqrtf(qr[0] * qr[0] + qr[1] * qr[1] + qr[2] * qr[2] + qr[3] * qr[3]);
+  const float qw = qr[0] * qn, qx = qr[1] * qn, qy = qr[2] * qn, qz = qr[3] * qn;
+  float Rq[3][3] = {{1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy)},
+                    {2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx)},
+                    {2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)}};
+  const float s[3] = {sx, sy, sz};
+  float Mm[3][3];  // Rq diag(s)
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) Mm[r][c] = Rq[r][c] * s[c];
+  float S3[3][3];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) S3[r][c] = Mm[r][0] * Mm[c][0] + Mm[r][1] * Mm[c][1] + Mm[r][2] * Mm[c][2];
+
+  float dmu[3] = {0.f, 0.f, 0.f};
+  float dS3[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  float dsh[16][3];
+  for (int c = 0; c < 16; ++c) dsh[c][0] = dsh[c][1] = dsh[c][2] = 0.f;
+
+  for (int k = 0; k < g.K; ++k) {
+    const size_t rec = (size_t)k * a.M + i;
+    // per-view means (Eq. 5)
+    for (int l = 0; l < g.C; ++l) {
+      const float gx = gr.grad_means2d[2 * (rec * g.C + l)];
+      const float gy = gr.grad_means2d[2 * (rec * g.C + l) + 1];
+      if (gx == 0.f && gy == 0.f) continue;
+      const int j = min(k * g.C + l, g.N - 1);
+      const float* cj = cams.c[j];
+      const float3 p = cam_point(cj, mx, my, mz);
+      const float iz = 1.f / p.z;
+      const float dpx = cj[12] * iz * gx, dpy = cj[13] * iz * gy;
+      const float dpz = -(cj[12] * p.x * gx + cj[13] * p.y * gy) * iz * iz;
+      dmu[0] += cj[0] * dpx + cj[3] * dpy + cj[6] * dpz;
+      dmu[1] += cj[1] * dpx + cj[4] * dpy + cj[7] * dpz;
+      dmu[2] += cj[2] * dpx + cj[5] * dpy + cj[8] * dpz;
+    }
+    const float4 gcon = reinterpret_cast<const float4*>(gr.grad_conic)[rec];
+    const float4 gcol = reinterpret_cast<const float4*>(gr.grad_color)[rec];
+    const float4 ct = reinterpret_cast<const float4*>(a.color_tau)[rec];
+    if (!(ct.w >= 0.f)) continue;  // culled for this cluster
+    const int jr = min(k * g.C + g.C / 2, g.N - 1);
+    const float* cr = cams.c[jr];
+    const float3 p = cam_point(cr, mx, my, mz);
+    // ---- colour (SH at the representative camera centre) ----
+    if (gcol.x != 0.f || gcol.y != 0.f || gcol.z != 0.f) {
+      const float cpx = -(cr[0] * cr[9] + cr[3] * cr[10] + cr[6] * cr[11]);
+      const float cpy = -(cr[1] * cr[9] + cr[4] * cr[10] + cr[7] * cr[11]);
+      const float cpz = -(cr[2] * cr[9] + cr[5] * cr[10] + cr[8] * cr[11]);
+      const float ux = mx - cpx, uy = my - cpy, uz = mz - cpz;
+      const float inv = rsqrtf(ux * ux + uy * uy + uz * uz);
+      const float x = ux * inv, y = uy * inv, z = uz * inv;
+      const float xx = x * x, yy = y * y, zz = z * z;
+      const float b[16] = {kC0, -kC1 * y, kC1 * z, -kC1 * x, kC2a * x * y, -kC2a * y * z,
+                           kC2b * (2.f * zz - xx - yy), -kC2a * x * z, kC2c * (xx - yy),
+                           -kC3a * y * (3.f * xx - yy), kC3b * x * y * z, -kC3c * y * (4.f * zz - xx - yy),
+                           kC3d * z * (2.f * zz - 3.f * xx - 3.f * yy), -kC3c * x * (4.f * zz - xx - yy),
+                           kC3e * z * (xx - yy), -kC3a * x * (xx - 3.f * yy)};
+      const float bx[16] = {0.f, 0.f, 0.f, -kC1, kC2a * y, 0.f, -2.f * kC2b * x, -kC2a * z, 2.f * kC2c * x,
+                            -6.f * kC3a * x * y, kC3b * y * z, 2.f * kC3c * x * y, -6.f * kC3d * x * z,
+                            -kC3c * (4.f * zz - 3.f * xx - yy), 2.f * kC3e * x * z, -kC3a * (3.f * xx - 3.f * yy)};
+      const float by[16] = {0.f, -kC1, 0.f, 0.f, kC2a * x, -kC2a * z, -2.f * kC2b * y, 0.f, -2.f * kC2c * y,
+                            -kC3a * (3.f * xx - 3.f * yy), kC3b * x * z, -kC3c * (4.f * zz - xx - 3.f * yy),
+                            -6.f * kC3d * y * z, 2.f * kC3c * x * y, -2.f * kC3e * y * z, 6.f * kC3a * x * y};
+      const float bz[16] = {0.f, 0.f, kC1, 0.f, 0.f, -kC2a * y, 4.f * kC2b * z, -kC2a * x, 0.f, 0.f,
+                            kC3b * x * y, -8.f * kC3c * y * z, kC3d * (6.f * zz - 3.f * xx - 3.f * yy),
+                            -8.f * kC3c * x * z, kC3e * (xx - yy), 0.f};
+      const float gc[3] = {gcol.x, gcol.y, gcol.z};
+      float ddx = 0.f, ddy = 0.f, ddz = 0.f;
+      for (int u = 0; u < 3; ++u) {
+        float v = 0.5f;
+        for (int c = 0; c < ncoef; ++c) v += b[c] * shs[((size_t)i * ncoef + c) * 3 + u];
+        if (!(v > 0.f)) continue;  // clamped at zero: no gradient
+        for (int c = 0; c < ncoef; ++c) {
+          dsh[c][u] += b[c] * gc[u];
+          const float sv = shs[((size_t)i * ncoef + c) * 3 + u] * gc[u];
+          ddx += bx[c] * sv;
+          ddy += by[c] * sv;
+          ddz += bz[c] * sv;
+        }
+      }
+      // through the normalisation of the direction
+      const float dot = x * ddx + y * ddy + z * ddz;
+      dmu[0] += (ddx - x * dot) * inv;
+      dmu[1] += (ddy - y * dot) * inv;
+      dmu[2] += (ddz - z * dot) * inv;
+    }
+    // ---- covariance: conic -> Sigma2D -> (Sigma3D, Jacobian) ----
+    if (gcon.x == 0.f && gcon.y == 0.f && gcon.z == 0.f) continue;
+    const float fx = cr[12], fy = cr[13];
+    const float limx = 1.3f * (0.5f * (float)g.W / fx);
+    const float limy = 1.3f * (0.5f * (float)g.H / fy);
+    const float iz = 1.f / p.z;
+    const float rx = p.x * iz, ry = p.y * iz;
+    const bool clx = rx < -limx || rx > limx, cly = ry < -limy || ry > limy;
+    const float txz = fminf(fmaxf(rx, -limx), limx);
+    const float tyz = fminf(fmaxf(ry, -limy), limy);
+    const float J[2][3] = {{fx * iz, 0.f, -fx * txz * iz}, {0.f, fy * iz, -fy * tyz * iz}};
+    float Tm[2][3];
+    for (int r = 0; r < 2; ++r)
+      for (int c = 0; c < 3; ++c) Tm[r][c] = J[r][0] * cr[c] + J[r][1] * cr[3 + c] + J[r][2] * cr[6 + c];
+    float TS[2][3];  // Tm S3
+    for (int r = 0; r < 2; ++r)
+      for (int c = 0; c < 3; ++c) TS[r][c] = Tm[r][0] * S3[0][c] + Tm[r][1] * S3[1][c] + Tm[r][2] * S3[2][c];
+    const float Sxx = TS[0][0] * Tm[0][0] + TS[0][1] * Tm[0][1] + TS[0][2] * Tm[0][2] + 0.3f;
+    const float Sxy = TS[0][0] * Tm[1][0] + TS[0][1] * Tm[1][1] + TS[0][2] * Tm[1][2];
+    const float Syy = TS[1][0] * Tm[1][0] + TS[1][1] * Tm[1][1] + TS[1][2] * Tm[1][2] + 0.3f;
+    const float det = Sxx * Syy - Sxy * Sxy;
+    const float id2 = 1.f / (det * det);
+    // conic (a, b, c) = (Syy, -Sxy, Sxx) / det
+    const float da = gcon.x, db = gcon.y, dc = gcon.z;
+    const float dSxx = -Syy * Syy * id2 * da + Sxy * Syy * id2 * db + (1.f / det - Sxx * Syy * id2) * dc;
+    const float dSyy = (1.f / det - Sxx * Syy * id2) * da + Sxy * Sxx * id2 * db - Sxx * Sxx * id2 * dc;
+    const float dSxy = 2.f * Sxy * Syy * id2 * da + (-1.f / det - 2.f * Sxy * Sxy * id2) * db +
+                       2.f * Sxy * Sxx * id2 * dc;
+    // symmetric matrix gradient of Sigma2D
+    const float Gm[2][2] = {{dSxx, 0.5f * dSxy}, {0.5f * dSxy, dSyy}};
+    // dSigma3D += Tm^T G Tm
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c)
+        dS3[r][c] += Tm[0][r] * (Gm[0][0] * Tm[0][c] + Gm[0][1] * Tm[1][c]) +
+                     Tm[1][r] * (Gm[1][0] * Tm[0][c] + Gm[1][1] * Tm[1][c]);
+    // dTm = 2 G Tm S3, dJ = dTm W^T
+    float dTm[2][3];
+    for (int r = 0; r < 2; ++r)
+      for (int c = 0; c < 3; ++c) dTm[r][c] = 2.f * (Gm[r][0] * TS[0][c] + Gm[r][1] * TS[1][c]);
+    float dJ[2][3];
+    for (int r = 0; r < 2; ++r)
+      for (int c = 0; c < 3; ++c) dJ[r][c] = dTm[r][0] * cr[3 * c] + dTm[r][1] * cr[3 * c + 1] + dTm[r][2] * cr[3 * c + 2];
+    // J00 = fx/z, J02 = -fx txz / z, J11 = fy/z, J12 = -fy tyz / z
+    float dpx = 0.f, dpy = 0.f, dpz = 0.f;
+    dpz += dJ[0][0] * (-fx * iz * iz) + dJ[1][1] * (-fy * iz * iz);
+    if (clx) {
+      dpz += dJ[0][2] * (fx * txz * iz * iz);
+    } else {
+      dpx += dJ[0][2] * (-fx * iz * iz);
+      dpz += dJ[0][2] * (2.f * fx * p.x * iz * iz * iz);
+    }
+    if (cly) {
+      dpz += dJ[1][2] * (fy * tyz * iz * iz);
+    } else {
+      dpy += dJ[1][2] * (-fy * iz * iz);
+      dpz += dJ[1][2] * (2.f * fy * p.y * iz * iz * iz);
+    }
+    dmu[0] += cr[0] * dpx + cr[3] * dpy + cr[6] * dpz;
+    dmu[1] += cr[1] * dpx + cr[4] * dpy + cr[7] * dpz;
+    dmu[2] += cr[2] * dpx + cr[5] * dpy + cr[8] * dpz;
+  }
+  // Sigma3D = Mm Mm^T -> dMm = 2 dS3_sym Mm (dS3 is accumulated symmetric)
+  float dM[3][3];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c)
+      dM[r][c] = (dS3[r][0] + dS3[0][r]) * Mm[0][c] + (dS3[r][1] + dS3[1][r]) * Mm[1][c] +
+                 (dS3[r][2] + dS3[2][r]) * Mm[2][c];
+  float dR[3][3];
+  float ds[3] = {0.f, 0.f, 0.f};
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      dR[r][c] = dM[r][c] * s[c];
+      ds[c] += dM[r][c] * Rq[r][c];
+    }
+  const float dw = 2.f * (-qz * dR[0][1] + qy * dR[0][2] + qz * dR[1][0] - qx * dR[1][2] - qy * dR[2][0] + qx * dR[2][1]);
+  const float dxq = 2.f * (qy * dR[0][1] + qz * dR[0][2] + qy * dR[1][0] - 2.f * qx * dR[1][1] - qw * dR[1][2] +
+                           qz * dR[2][0] + qw * dR[2][1] - 2.f * qx * dR[2][2]);
+  const float dyq = 2.f * (-2.f * qy * dR[0][0] + qx * dR[0][1] + qw * dR[0][2] + qx * dR[1][0] + qz * dR[1][2] -
+                           qw * dR[2][0] + qz * dR[2][1] - 2.f * qy * dR[2][2]);
+  const float dzq = 2.f * (-2.f * qz * dR[0][0] - qw * dR[0][1] + qx * dR[0][2] + qw * dR[1][0] - 2.f * qz * dR[1][1] +
+                           qy * dR[1][2] + qx * dR[2][0] + qy * dR[2][1]);
+  const float dqn[4] = {dw, dxq, dyq, dzq};
+  const float qv[4] = {qw, qx, qy, qz};
+  const float dd = qv[0] * dqn[0] + qv[1] * dqn[1] + qv[2] * dqn[2] + qv[3] * dqn[3];
+  for (int c = 0; c < 4; ++c) out.quats[4 * i + c] = (dqn[c] - qv[c] * dd) * qn;
+  for (int c = 0; c < 3; ++c) {
+    out.means[3 * i + c] = dmu[c];
+    out.scales[3 * i + c] = ds[c];
+  }
+  out.opacities[i] = gr.grad_opac[i];
+  for (int c = 0; c < ncoef; ++c)
+    for (int u = 0; u < 3; ++u) out.sh[((size_t)i * ncoef + c) * 3 + u] = dsh[c][u];
+  (void)o;
+  (void)kLn2;
+}
+
+}  // namespace
+
+cudaError_t launch_blend_backward(const PanelGeom& g, const BlendArgs& a, const BlendGrads& gr,
+                                  cudaStream_t s) {
+  if ((int64_t)g.K * g.T == 0) return cudaSuccess;
+  const int need = a.max_segment > 0 ? a.max_segment : 1;
+  const int block = min(256, ((need + 31) / 32) * 32);
+  const size_t smem = (size_t)block * (2 * sizeof(float4) + g.C * sizeof(float2) + sizeof(uint32_t));
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_blend_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_blend_backward<<<(unsigned)((int64_t)g.K * g.T), block, smem, s>>>(g, a, gr);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_project_backward(const PanelGeom& g, const CamTable& cams, const ProjectArgs& a,
+                                    const BlendGrads& gr, const ParamGrads& out, cudaStream_t s) {
+  if (a.M == 0) return cudaSuccess;
+  k_project_backward<<<(unsigned)((a.M + 127) / 128), 128, 0, s>>>(g, cams, a, gr, out);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace lfd

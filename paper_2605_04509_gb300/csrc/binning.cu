@@ -174,7 +174,7 @@ __device__ __forceinline__ uint32_t bin_union(const PanelGeom& pg, const BinQ& q
 // emit pass need not redo the geometry: header = ty0 | c0 << 16 | rows << 32
 // | overflow << 40, then one 64-tile mask per row. Items whose union spans
 // more than kDescRows rows or 64 tile columns are marked overflow and redone.
-constexpr int kDescRows = 7;
+constexpr int kDescRows = 15;
 struct __align__(16) BinDesc {
   unsigned long long header;
   unsigned long long mask[kDescRows];
@@ -193,33 +193,119 @@ __global__ void k_item_keys(PanelGeom g, int64_t M, const float* __restrict__ de
   vals[r] = (uint32_t)r;
 }
 
-__global__ void k_bin_count(PanelGeom g, int64_t M, const float2* __restrict__ means2d,
-                            const float4* __restrict__ conic_opacity,
-                            const float4* __restrict__ color_tau, const uint32_t* __restrict__ order,
-                            int64_t n_items, uint32_t* __restrict__ counts,
-                            BinDesc* __restrict__ desc) {
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n_items) return;
-  const uint32_t r = order ? order[s] : (uint32_t)s;
-  const float4 co = conic_opacity[r];
-  BinQ q;
-  uint32_t n = 0;
-  unsigned long long header = 0ull;
-  if (bin_prep(co.x, co.y, co.z, color_tau[r].w, q)) {
-    const float2* means = means2d + (size_t)r * g.C;
-    int ty0, ty1, c0, c1;
-    bin_extent(g, q, means, ty0, ty1, c0, c1);
-    const int rows = ty1 >= ty0 ? ty1 - ty0 + 1 : 0;
-    const bool fits = rows <= kDescRows && (rows == 0 || c1 - c0 < 64);
-    n = bin_rows(g, q, means, ty0, ty1, c0, c1, [&](int ty, int, unsigned long long mask) {
-      if (desc && fits) desc[s].mask[ty - ty0] = mask;
-    });
-    header = rows == 0 ? 0ull
-                       : ((unsigned long long)ty0 | ((unsigned long long)c0 << 16) |
-                          ((unsigned long long)rows << 32) | ((unsigned long long)(fits ? 0 : 1) << 40));
+__device__ __forceinline__ BinQ shfl_q(const BinQ& q, int src) {
+  BinQ o;
+  o.a = __shfl_sync(0xffffffffu, q.a, src);
+  o.b = __shfl_sync(0xffffffffu, q.b, src);
+  o.c = __shfl_sync(0xffffffffu, q.c, src);
+  o.tau = __shfl_sync(0xffffffffu, q.tau, src);
+  o.det = __shfl_sync(0xffffffffu, q.det, src);
+  o.hx = __shfl_sync(0xffffffffu, q.hx, src);
+  o.hy = __shfl_sync(0xffffffffu, q.hy, src);
+  o.ys = __shfl_sync(0xffffffffu, q.ys, src);
+  o.ia = __shfl_sync(0xffffffffu, q.ia, src);
+  return o;
+}
+
+// Exclusive prefix over the warp's lanes; *total receives the sum.
+__device__ __forceinline__ int warp_exclusive(int v, int lane, int* total) {
+  int incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
   }
-  counts[s] = n;
-  if (desc) desc[s].header = header;
+  *total = __shfl_sync(0xffffffffu, incl, 31);
+  return incl - v;
+}
+
+// Lane of the warp owning work unit u, given each lane's first unit
+// (non-decreasing over lanes): the last lane whose first unit is <= u.
+__device__ __forceinline__ int unit_owner(int ubase, int u) {
+  int j = 0;
+#pragma unroll
+  for (int st = 16; st > 0; st >>= 1) {
+    const int cand = j + st;
+    const int ub = __shfl_sync(0xffffffffu, ubase, cand & 31);
+    if (cand < 32 && ub <= u) j = cand;
+  }
+  return j;
+}
+
+constexpr int kBinWarps = 4;
+
+// Tile counts (and union descriptors) of the items. Each warp takes 32
+// items; their tile rows are dealt out to the lanes as separate work units,
+// so a large Gaussian does not hold up its warp. A unit unites the cluster's
+// views over one tile row. Items whose union is wider than 64 tile columns
+// are walked by their own lane.
+__global__ void __launch_bounds__(32 * kBinWarps)
+    k_bin_count(PanelGeom g, int64_t M, const float2* __restrict__ means2d,
+                const float4* __restrict__ conic_opacity, const float4* __restrict__ color_tau,
+                const uint32_t* __restrict__ order, int64_t n_items, uint32_t* __restrict__ counts,
+                BinDesc* __restrict__ desc) {
+  __shared__ uint32_t s_n[kBinWarps][32];
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool in = s < n_items;
+  uint32_t r = 0;
+  BinQ q = {};
+  bool ok = false;
+  int ty0 = 0, ty1 = -1, c0 = 0, c1 = -1;
+  if (in) {
+    r = order ? order[s] : (uint32_t)s;
+    const float4 co = conic_opacity[r];
+    ok = bin_prep(co.x, co.y, co.z, color_tau[r].w, q);
+    if (ok) bin_extent(g, q, means2d + (size_t)r * g.C, ty0, ty1, c0, c1);
+  }
+  const int rows = ok && ty1 >= ty0 ? ty1 - ty0 + 1 : 0;
+  const bool wide = rows > 0 && c1 - c0 >= 64;
+  const bool fits = rows <= kDescRows && !wide;
+  s_n[warp][lane] = 0;
+  uint32_t n_self = 0;
+  if (wide)
+    n_self = bin_rows(g, q, means2d + (size_t)r * g.C, ty0, ty1, c0, c1,
+                      [](int, int, unsigned long long) {});
+  int U;
+  const int ubase = warp_exclusive(wide ? 0 : rows, lane, &U);
+  __syncwarp();
+  const int64_t s_warp0 = s - lane;
+  for (int b = 0; b < U; b += 32) {
+    const int u = b + lane;
+    const int j = unit_owner(ubase, u);
+    const int rr = u - __shfl_sync(0xffffffffu, ubase, j);
+    const BinQ qj = shfl_q(q, j);
+    const uint32_t rj = __shfl_sync(0xffffffffu, r, j);
+    const int ty0j = __shfl_sync(0xffffffffu, ty0, j);
+    const int c0j = __shfl_sync(0xffffffffu, c0, j);
+    const bool fitsj = __shfl_sync(0xffffffffu, fits, j);
+    if (u < U) {
+      const float2* mj = means2d + (size_t)rj * g.C;
+      const int ty = ty0j + rr;
+      unsigned long long mask = 0ull;
+      for (int l = 0; l < g.C; ++l) {
+        const float2 m = mj[l];
+        BinV v;
+        bin_view(qj, m.x, m.y, g.W, g.H, v);
+        int a, bb;
+        if (!bin_row(qj, v, ty, g.TW, g.TH, a, bb)) continue;
+        const int len = bb - a + 1;
+        const unsigned long long bits = len == 64 ? ~0ull : ((1ull << len) - 1ull);
+        mask |= bits << (a - c0j);
+      }
+      atomicAdd(&s_n[warp][j], (uint32_t)__popcll(mask));
+      if (desc && fitsj) desc[s_warp0 + j].mask[rr] = mask;
+    }
+  }
+  __syncwarp();
+  if (in) {
+    counts[s] = wide ? n_self : s_n[warp][lane];
+    if (desc)
+      desc[s].header = rows == 0 ? 0ull
+                                 : ((unsigned long long)ty0 | ((unsigned long long)c0 << 16) |
+                                    ((unsigned long long)rows << 32) |
+                                    ((unsigned long long)(fits ? 0 : 1) << 40));
+  }
 }
 
 __global__ void k_bin_emit(PanelGeom g, int64_t M, const float2* __restrict__ means2d,
@@ -278,6 +364,117 @@ __global__ void k_bin_emit(PanelGeom g, int64_t M, const float2* __restrict__ me
   }
 }
 
+// Emission from the count pass's union descriptors (indexed by item r). Each
+// lane expands its own item's tiles (from the descriptor, or from the
+// geometry when the union did not fit one) into a per-warp staging buffer in
+// shared memory at the item's offset relative to the warp's first item; the
+// warp then copies the buffer out with consecutive lanes on consecutive
+// addresses, so the global stores coalesce. Warps whose items hold more
+// pairs than the buffer write straight to global memory. Positions and
+// contents equal the plain per-item emission's.
+constexpr int kEmitWarps = 4;
+
+template <typename KeyT>
+struct EmitCap {
+  static constexpr int value = (6144 / (int)(sizeof(KeyT) + 4)) & ~31;  // ~24 KB per block
+};
+
+template <typename KeyT>
+__global__ void __launch_bounds__(32 * kEmitWarps)
+    k_bin_emit_staged(PanelGeom g, int64_t M, const float2* __restrict__ means2d,
+                      const float4* __restrict__ conic_opacity, const float4* __restrict__ color_tau,
+                      const float* __restrict__ depth, const uint32_t* __restrict__ order,
+                      int64_t n_items, const uint32_t* __restrict__ counts,
+                      const uint32_t* __restrict__ offsets, KeyT* __restrict__ keys,
+                      uint32_t* __restrict__ vals, const BinDesc* __restrict__ desc) {
+  constexpr int CAP = EmitCap<KeyT>::value;
+  constexpr bool kWide = sizeof(KeyT) == 8;
+  __shared__ KeyT s_key[kEmitWarps][CAP];
+  __shared__ uint32_t s_val[kEmitWarps][CAP];
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool in = s < n_items;
+  uint32_t r = 0, n = 0, pos = 0;
+  unsigned long long h = 0ull;
+  if (in) {
+    r = order ? order[s] : (uint32_t)s;
+    n = counts[s];
+    pos = offsets[s];
+    if (n) h = desc[r].header;
+  }
+  const unsigned valid = __ballot_sync(0xffffffffu, in);
+  if (!valid) return;
+  const int last = 31 - __clz((int)valid);
+  const uint32_t wbase = __shfl_sync(0xffffffffu, pos, 0);
+  const uint32_t wend = __shfl_sync(0xffffffffu, pos + n, last);
+  const uint32_t total = wend - wbase;
+  const bool staged = total <= (uint32_t)CAP;
+  KeyT* kdst = staged ? &s_key[warp][0] : keys;
+  uint32_t* vdst = staged ? &s_val[warp][0] : vals;
+  const uint32_t shift_out = staged ? wbase : 0u;
+  const int shift = kWide ? 32 + g.bit_k : g.bit_k;
+  // unions that did not fit a descriptor: the owner lane redoes the geometry
+  const bool redo = in && n && ((h >> 40) & 1ull);
+  if (redo) {
+    const uint32_t k = (uint32_t)(r / M);
+    const uint32_t i = (uint32_t)(r - (uint64_t)k * M);
+    const uint64_t lo = kWide ? (((uint64_t)k << 32) | __float_as_uint(depth[r])) : 0ull;
+    uint32_t p = pos - shift_out;
+    const float4 co = conic_opacity[r];
+    BinQ q;
+    if (bin_prep(co.x, co.y, co.z, color_tau[r].w, q))
+      bin_union(g, q, means2d + (size_t)r * g.C, [&](int t) {
+        kdst[p] = kWide ? (KeyT)(((uint64_t)t << shift) | lo) : (KeyT)(((uint32_t)t << shift) | k);
+        vdst[p] = i;
+        ++p;
+      });
+  }
+  // the other items' tile rows are dealt out to the lanes
+  const int units = (in && n && !redo) ? (int)((h >> 32) & 0xffull) : 0;
+  int U;
+  const int ubase = warp_exclusive(units, lane, &U);
+  for (int b = 0; b < U; b += 32) {
+    const int u = b + lane;
+    const int j = unit_owner(ubase, u);
+    const int rr = u - __shfl_sync(0xffffffffu, ubase, j);
+    const uint32_t rj = __shfl_sync(0xffffffffu, r, j);
+    const uint32_t pj = __shfl_sync(0xffffffffu, pos, j);
+    const unsigned long long hj =
+        ((unsigned long long)__shfl_sync(0xffffffffu, (uint32_t)(h >> 32), j) << 32) |
+        __shfl_sync(0xffffffffu, (uint32_t)h, j);
+    if (u < U) {
+      const int ty0 = (int)(hj & 0xffffull), c0 = (int)((hj >> 16) & 0xffffull);
+      const uint32_t k = (uint32_t)(rj / M);
+      const uint32_t i = (uint32_t)(rj - (uint64_t)k * M);
+      const uint64_t lo = kWide ? (((uint64_t)k << 32) | __float_as_uint(depth[rj])) : 0ull;
+      uint32_t p = pj - shift_out;
+      for (int x = 0; x < rr; ++x) p += (uint32_t)__popcll(desc[rj].mask[x]);
+      unsigned long long mask = desc[rj].mask[rr];
+      while (mask) {
+        const int bit = __ffsll((long long)mask) - 1;
+        mask &= mask - 1ull;
+        const uint32_t t = (uint32_t)((ty0 + rr) * g.TX + c0 + bit);
+        kdst[p] = kWide ? (KeyT)(((uint64_t)t << shift) | lo) : (KeyT)((t << shift) | k);
+        vdst[p] = i;
+        ++p;
+      }
+    }
+  }
+  if (staged) {
+    __syncwarp();
+    for (uint32_t q = lane; q < total; q += 32) {
+      keys[wbase + q] = s_key[warp][q];
+      vals[wbase + q] = s_val[warp][q];
+    }
+  }
+}
+
+__global__ void k_gather_u32(const uint32_t* __restrict__ src, const uint32_t* __restrict__ idx,
+                             int64_t n, uint32_t* __restrict__ dst) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) dst[s] = src[idx[s]];
+}
+
 __global__ void k_ranges(PanelGeom g, int64_t P, const uint32_t* __restrict__ keys32,
                          const uint64_t* __restrict__ keys64, uint2* __restrict__ ranges) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -314,7 +511,7 @@ cudaError_t launch_bin_count(const PanelGeom& g, int64_t M, const float* means2d
                              const uint32_t* order, int64_t n_items, uint32_t* counts, void* desc,
                              cudaStream_t s) {
   if (n_items == 0) return cudaSuccess;
-  k_bin_count<<<blocks_for(n_items, 128), 128, 0, s>>>(
+  k_bin_count<<<blocks_for(n_items, 32 * kBinWarps), 32 * kBinWarps, 0, s>>>(
       g, M, reinterpret_cast<const float2*>(means2d),
       reinterpret_cast<const float4*>(conic_opacity), reinterpret_cast<const float4*>(color_tau),
       order, n_items, counts, reinterpret_cast<BinDesc*>(desc));
@@ -332,6 +529,37 @@ cudaError_t launch_bin_emit(const PanelGeom& g, int64_t M, const float* means2d,
       g, M, reinterpret_cast<const float2*>(means2d),
       reinterpret_cast<const float4*>(conic_opacity), reinterpret_cast<const float4*>(color_tau),
       depth, order, n_items, offsets, keys32, keys64, vals, reinterpret_cast<const BinDesc*>(desc));
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bin_emit_coop(const PanelGeom& g, int64_t M, const float* means2d,
+                                 const float* conic_opacity, const float* color_tau,
+                                 const float* depth, const uint32_t* order, int64_t n_items,
+                                 const uint32_t* counts, const uint32_t* offsets, uint32_t* keys32,
+                                 uint64_t* keys64, uint32_t* vals, const void* desc, cudaStream_t s) {
+  if (n_items == 0) return cudaSuccess;
+  const unsigned blocks = blocks_for(n_items, 32 * kEmitWarps);
+  if (keys64)
+    k_bin_emit_staged<uint64_t><<<blocks, 32 * kEmitWarps, 0, s>>>(
+        g, M, reinterpret_cast<const float2*>(means2d),
+        reinterpret_cast<const float4*>(conic_opacity), reinterpret_cast<const float4*>(color_tau),
+        depth, order, n_items, counts, offsets, keys64, vals,
+        reinterpret_cast<const BinDesc*>(desc));
+  else
+    k_bin_emit_staged<uint32_t><<<blocks, 32 * kEmitWarps, 0, s>>>(
+        g, M, reinterpret_cast<const float2*>(means2d),
+        reinterpret_cast<const float4*>(conic_opacity), reinterpret_cast<const float4*>(color_tau),
+        depth, order, n_items, counts, offsets, keys32, vals,
+        reinterpret_cast<const BinDesc*>(desc));
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_u32(const uint32_t* src, const uint32_t* idx, int64_t n, uint32_t* dst,
+                              cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_gather_u32<<<blocks_for(n, 256), 256, 0, s>>>(src, idx, n, dst);
   note_launches(1);
   return cudaGetLastError();
 }

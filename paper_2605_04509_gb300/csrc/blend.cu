@@ -15,8 +15,13 @@
 // bit set are compacted (warp ballots) into an index list; each subpixel walks
 // only its own view's list. The union over the cluster's views (Alg. 2) keeps
 // the other entries in the list, but they cannot reach alpha >= 1/255 for
-// this view, so skipping them leaves every result bit-identical. Grid order is cluster-major so that one cluster's
-// attributes stay resident in L2 while its tiles are blended.
+// this view, so skipping them leaves every result bit-identical. Means are
+// staged view-major ([view][entry]) so that staging stores and per-view reads
+// do not collide in shared-memory banks. An entry whose exponent lies below
+// log2(1 / (255 o)) (less a 1e-4 margin) is skipped before the exp2: it cannot
+// reach alpha >= 1/255. Each thread owns two subpixels of the run. Grid order
+// is cluster-major so that one cluster's attributes stay resident in L2 while
+// its tiles are blended.
 #include "lfd_internal.h"
 
 namespace lfd {
@@ -41,7 +46,7 @@ __global__ void __launch_bounds__(256) k_blend(PanelGeom g, BlendArgs a) {
   const int C = g.C;
   float4* s_co = smem;        // conic * (-log2(e) / 2, -log2(e), -log2(e) / 2), opacity
   float4* s_col = smem + NB;  // colour
-  float2* s_mean = reinterpret_cast<float2*>(smem + 2 * NB);        // [NB][C]
+  float2* s_mean = reinterpret_cast<float2*>(smem + 2 * NB);        // [C][NB]
   uint16_t* s_idx = reinterpret_cast<uint16_t*>(s_mean + NB * C);   // [C][NB]
   int* s_cnt = reinterpret_cast<int*>(s_idx + ((C * NB + 1) & ~1));  // [C][NW + 1]
 
@@ -109,14 +114,15 @@ __global__ void __launch_bounds__(256) k_blend(PanelGeom g, BlendArgs a) {
       const float4 co = reinterpret_cast<const float4*>(a.conic_opacity)[rec];
       const float4 ct = reinterpret_cast<const float4*>(a.color_tau)[rec];
       s_co[threadIdx.x] = make_float4(-0.5f * kLog2e * co.x, -kLog2e * co.y, -0.5f * kLog2e * co.z, co.w);
-      s_col[threadIdx.x] = ct;
+      // w: log2 of the opacity ratio at which alpha reaches 1/255 (skip below)
+      s_col[threadIdx.x] = make_float4(ct.x, ct.y, ct.z, -log2f(255.f * co.w) - 1e-4f);
       const float det = co.x * co.z - co.y * co.y;
       const float hx = sqrtf(fmaxf(ct.w * co.z / det, 0.f));
       const float hy = sqrtf(fmaxf(ct.w * co.x / det, 0.f));
       const float2* mp = reinterpret_cast<const float2*>(a.means2d) + rec * C;
       for (int l = 0; l < C; ++l) {
         const float2 mu = mp[l];
-        s_mean[threadIdx.x * C + l] = mu;
+        s_mean[l * NB + threadIdx.x] = mu;
         const bool hit = (mu.x + hx >= bx0) && (mu.x - hx <= bx1) && (mu.y + hy >= by0) &&
                          (mu.y - hy <= by1);
         mask |= (uint32_t)hit << l;
@@ -155,11 +161,12 @@ __global__ void __launch_bounds__(256) k_blend(PanelGeom g, BlendArgs a) {
         const int gi = idx[q];
         if (COUNT) ++n_eval;
         const float4 co = s_co[gi];
-        const float2 mu = s_mean[gi * C + slot[m]];
+        const float4 cl = s_col[gi];
+        const float2 mu = s_mean[slot[m] * NB + gi];
         const float dx = px[m] - mu.x;
         const float dy = py[m] - mu.y;
         const float power = co.x * dx * dx + co.z * dy * dy + co.y * dx * dy;
-        if (power > 0.f) continue;
+        if (power > 0.f || power < cl.w) continue;
         const float v = co.w * ex2_approx(power);
         if (!(v >= kAlphaMin)) continue;
         const float alpha = fminf(kAlphaMax, v);
@@ -169,7 +176,6 @@ __global__ void __launch_bounds__(256) k_blend(PanelGeom g, BlendArgs a) {
           stop = gi;
           break;
         }
-        const float4 cl = s_col[gi];
         const float c = ch[m] == 0 ? cl.x : (ch[m] == 1 ? cl.y : cl.z);
         acc[m] += c * alpha * T[m];
         T[m] = Tn;
@@ -224,7 +230,7 @@ cudaError_t launch_r(const PanelGeom& g, const BlendArgs& a, int block, cudaStre
 cudaError_t launch_blend(const PanelGeom& g, const BlendArgs& a, cudaStream_t s) {
   if ((int64_t)g.K * g.T == 0) return cudaSuccess;
   const int need = a.max_segment > 0 ? a.max_segment : 1;
-  int R = 1;
+  int R = 2;
   while (R < 8 && (need + R - 1) / R > 256) R *= 2;
   int block = (need + R - 1) / R;
   block = ((block + 31) / 32) * 32;

@@ -96,16 +96,19 @@ struct lfd_plan {
   // per-frame scratch
   DevBuf proj_means, proj_co, proj_ct, proj_depth;
   DevBuf item_key[2], item_val[2];
-  DevBuf counts, offsets, scan_tmp, bin_desc;
+  DevBuf counts, counts_nat, offsets, scan_tmp, bin_desc;
   DevBuf pair_key[2], pair_val[2];
   DevBuf radix_tmp;
   DevBuf ranges;
   DevBuf small;  // [0] total pairs, [1] eval counter
   DevBuf host_in[5];  // device copies of host Gaussians (lfd_render_host)
   DevBuf image;       // device image for lfd_render_host
+  DevBuf g_means2d, g_conic, g_color, g_opac;  // backward scratch
   unsigned long long* h_small = nullptr;  // pinned
   // last frame
   int64_t last_P = -1;
+  int64_t last_M = -1;
+  bool last_from_render = false;
   int last_key_buf = 0;
   int last_val_buf = 0;
   int last_sort_mode = 0;
@@ -120,6 +123,10 @@ struct lfd_plan {
   bool ev_has_project[2] = {false, false};
   double acc_ms[4] = {0, 0, 0, 0};
   int64_t acc_frames = 0;
+  // full-frame baseline: a child plan with one view per cluster whose blend
+  // renders whole per-view images (created on first use)
+  bool fullframe = false;
+  lfd_plan* ff_child = nullptr;
 };
 
 namespace {
@@ -149,6 +156,8 @@ int plan_view(const lfd_plan* p, PlanView* out) {
   out->seg = p->seg;
   out->max_segment = p->max_segment;
   out->sort_mode = p->opts.sort_mode;
+  out->remap = p->opts.remap;
+  out->V = p->V;
   out->bg[0] = p->opts.bg[0];
   out->bg[1] = p->opts.bg[1];
   out->bg[2] = p->opts.bg[2];
@@ -189,6 +198,7 @@ const char* lfd_last_error(void) { return g_last_error; }
 
 void lfd_plan_destroy(lfd_plan* p) {
   if (!p) return;
+  if (p->ff_child) lfd_plan_destroy(p->ff_child);
   cudaSetDevice(p->device);
   cudaDeviceSynchronize();
   cudaFree(p->V);
@@ -197,10 +207,11 @@ void lfd_plan_destroy(lfd_plan* p) {
   cudaFree(p->seg);
   DevBuf* bufs[] = {&p->proj_means, &p->proj_co,   &p->proj_ct,     &p->proj_depth,
                     &p->item_key[0], &p->item_key[1], &p->item_val[0], &p->item_val[1],
-                    &p->counts,     &p->offsets,   &p->scan_tmp,    &p->bin_desc,  &p->pair_key[0],
+                    &p->counts,     &p->counts_nat, &p->offsets,   &p->scan_tmp,    &p->bin_desc,  &p->pair_key[0],
                     &p->pair_key[1], &p->pair_val[0], &p->pair_val[1], &p->radix_tmp,
                     &p->ranges,     &p->small,     &p->host_in[0],  &p->host_in[1],
-                    &p->host_in[2], &p->host_in[3], &p->host_in[4], &p->image};
+                    &p->host_in[2], &p->host_in[3], &p->host_in[4], &p->image,
+                    &p->g_means2d,  &p->g_conic,   &p->g_color,     &p->g_opac};
   for (DevBuf* b : bufs) b->release();
   if (p->h_small) cudaFreeHost(p->h_small);
   for (auto& set : p->ev)
@@ -224,7 +235,7 @@ int lfd_plan_create(const lfd_panel* panel, const lfd_opts* opts, lfd_plan** out
     return fail(LFD_ERR_INVALID, "tile shape out of range");
   if (O.views_per_cluster < 1 || O.views_per_cluster > kMaxClusterViews)
     return fail(LFD_ERR_INVALID, "views_per_cluster not in [1, 32]");
-  if (O.remap != 1) return fail(LFD_ERR_INVALID, "only the view-coherent remap (remap = 1) is built");
+  if (O.remap != 0 && O.remap != 1) return fail(LFD_ERR_INVALID, "remap must be 0 or 1");
   if (O.sort_mode != LFD_SORT_DEPTH_FIRST && O.sort_mode != LFD_SORT_KEY64)
     return fail(LFD_ERR_INVALID, "unknown sort_mode");
 
@@ -341,12 +352,18 @@ static int check_gaussians(const lfd_plan* p, const lfd_gaussians* gs) {
   if (!gs) return fail(LFD_ERR_INVALID, "gaussians is NULL");
   if (gs->count < 0) return fail(LFD_ERR_INVALID, "negative Gaussian count");
   if (gs->sh_degree < 0 || gs->sh_degree > 3) return fail(LFD_ERR_INVALID, "sh_degree not in [0, 3]");
+  if (gs->attr_dtype != LFD_DTYPE_F32 && gs->attr_dtype != LFD_DTYPE_F16 &&
+      gs->attr_dtype != LFD_DTYPE_BF16)
+    return fail(LFD_ERR_INVALID, "unknown attr_dtype");
   if ((uint64_t)gs->count * (uint64_t)p->g.K >= (1ull << 32))
     return fail(LFD_ERR_CAPACITY, "count * clusters must stay below 2^32");
   if (gs->count > 0) {
     if (!gs->means || !gs->scales || !gs->quats || !gs->opacities || !gs->sh)
       return fail(LFD_ERR_INVALID, "NULL Gaussian attribute");
-    if (!aligned(gs->quats, 16)) return fail(LFD_ERR_INVALID, "quats must be 16-byte aligned");
+    const size_t es = gs->attr_dtype == LFD_DTYPE_F32 ? 4 : 2;
+    if (!aligned(gs->means, 4) || !aligned(gs->quats, es) || !aligned(gs->scales, es) ||
+        !aligned(gs->opacities, es) || !aligned(gs->sh, es))
+      return fail(LFD_ERR_INVALID, "Gaussian attributes misaligned for their type");
   }
   return LFD_OK;
 }
@@ -389,6 +406,7 @@ int lfd_project(lfd_plan* p, const lfd_gaussians* gs, const lfd_camera* cams, in
     a.sh = gs->sh;
     a.M = gs->count;
     a.sh_degree = gs->sh_degree;
+    a.attr_dtype = gs->attr_dtype;
     a.means2d = means2d;
     a.conic_opacity = conic_opacity;
     a.color_tau = color_tau;
@@ -430,6 +448,7 @@ static int render_projected_impl(lfd_plan* p, int64_t M, const float* means2d,
   // ---- stage 2: key generation ----
   if ((rc = p->counts.ensure((size_t)(n_items + 1) * 4)) != LFD_OK) return rc;
   if ((rc = p->offsets.ensure((size_t)(n_items + 1) * 4)) != LFD_OK) return rc;
+  if ((rc = p->counts_nat.ensure((size_t)(n_items + 1) * 4)) != LFD_OK) return rc;
   if ((rc = p->scan_tmp.ensure(scan_temp_bytes(n_items + 1))) != LFD_OK) return rc;
   if ((rc = p->bin_desc.ensure((size_t)(n_items + 1) * kBinDescBytes)) != LFD_OK) return rc;
   const uint32_t* order = nullptr;
@@ -448,8 +467,14 @@ static int render_projected_impl(lfd_plan* p, int64_t M, const float* means2d,
                             0, 32 + g.bit_k, p->radix_tmp.p, &alt, s));
     order = p->item_val[alt ? 1 : 0].as<uint32_t>();
   }
-  LFD_CUDA(launch_bin_count(g, M, means2d, conic_opacity, color_tau, order, n_items,
-                            p->counts.as<uint32_t>(), p->bin_desc.p, s));
+  // tile counts and union descriptors in natural (cluster, Gaussian) order:
+  // coalesced attribute reads; the counts are then gathered into the
+  // emission order for the offsets scan
+  LFD_CUDA(launch_bin_count(g, M, means2d, conic_opacity, color_tau, nullptr, n_items,
+                            order ? p->counts_nat.as<uint32_t>() : p->counts.as<uint32_t>(),
+                            p->bin_desc.p, s));
+  if (order)
+    LFD_CUDA(launch_gather_u32(p->counts_nat.as<uint32_t>(), order, n_items, p->counts.as<uint32_t>(), s));
   LFD_CUDA(scan_exclusive(p->counts.as<uint32_t>(), p->offsets.as<uint32_t>(), n_items, p->scan_tmp.p,
                           d_small, s));
   LFD_CUDA(cudaMemcpyAsync(p->h_small, d_small, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
@@ -464,10 +489,11 @@ static int render_projected_impl(lfd_plan* p, int64_t M, const float* means2d,
   }
   if ((rc = p->radix_tmp.ensure(radix_temp_bytes((int64_t)P))) != LFD_OK) return rc;
   if ((rc = p->ranges.ensure((size_t)g.T * g.K * sizeof(uint2))) != LFD_OK) return rc;
-  LFD_CUDA(launch_bin_emit(g, M, means2d, conic_opacity, color_tau, depth, order, n_items,
-                           p->offsets.as<uint32_t>(), key64 ? nullptr : p->pair_key[0].as<uint32_t>(),
-                           key64 ? p->pair_key[0].as<uint64_t>() : nullptr,
-                           p->pair_val[0].as<uint32_t>(), p->bin_desc.p, s));
+  LFD_CUDA(launch_bin_emit_coop(g, M, means2d, conic_opacity, color_tau, depth, order, n_items,
+                                p->counts.as<uint32_t>(), p->offsets.as<uint32_t>(),
+                                key64 ? nullptr : p->pair_key[0].as<uint32_t>(),
+                                key64 ? p->pair_key[0].as<uint64_t>() : nullptr,
+                                p->pair_val[0].as<uint32_t>(), p->bin_desc.p, s));
   if (timing) LFD_CUDA(cudaEventRecord(ev[2], s));
 
   // ---- stage 3: sort by (tile, cluster, depth) ----
@@ -505,7 +531,13 @@ static int render_projected_impl(lfd_plan* p, int64_t M, const float* means2d,
   ba.out = out_rgb;
   ba.eval_counter = counting ? d_small + 1 : nullptr;
   ba.max_segment = p->max_segment;
-  LFD_CUDA(launch_blend(g, ba, s));
+  ba.V = p->V;
+  if (p->fullframe)
+    LFD_CUDA(launch_blend_fullframe(g, ba, s));
+  else if (p->opts.remap)
+    LFD_CUDA(launch_blend(g, ba, s));
+  else
+    LFD_CUDA(launch_blend_raster(g, ba, s));
   if (timing) {
     LFD_CUDA(cudaEventRecord(ev[4], s));
     p->ev_pending[es] = true;
@@ -514,6 +546,8 @@ static int render_projected_impl(lfd_plan* p, int64_t M, const float* means2d,
   }
 
   p->last_P = (int64_t)P;
+  p->last_M = M;
+  p->last_from_render = projected_here;
   p->last_key_buf = kb;
   p->last_val_buf = kb;
   p->last_sort_mode = p->opts.sort_mode;
@@ -573,6 +607,101 @@ int lfd_render(lfd_plan* p, const lfd_gaussians* gs, const lfd_camera* cams, int
                                stats, true);
 }
 
+int lfd_render_backward(lfd_plan* p, const lfd_gaussians* gs, const lfd_camera* cams,
+                        int32_t num_cams, const float* grad_rgb, float* grad_means,
+                        float* grad_scales, float* grad_quats, float* grad_opacities,
+                        float* grad_sh, void* stream) {
+  if (!p) return fail(LFD_ERR_INVALID, "NULL plan");
+  int rc = check_gaussians(p, gs);
+  if (rc != LFD_OK) return rc;
+  if (gs->attr_dtype != LFD_DTYPE_F32) return fail(LFD_ERR_INVALID, "backward needs FP32 attributes");
+  if (!p->opts.remap || p->fullframe) return fail(LFD_ERR_INVALID, "backward needs the remapped plan");
+  if (!p->last_from_render || p->last_M != gs->count)
+    return fail(LFD_ERR_STATE, "backward needs the forward frame of lfd_render with the same Gaussians");
+  const int64_t M = gs->count;
+  if (M == 0) return LFD_OK;
+  if (!grad_rgb || !grad_means || !grad_scales || !grad_quats || !grad_opacities || !grad_sh)
+    return fail(LFD_ERR_INVALID, "NULL gradient buffer");
+  CamTable* t = new (std::nothrow) CamTable;
+  if (!t) return fail(LFD_ERR_OOM, "host allocation failed");
+  rc = fill_cams(p, cams, num_cams, t);
+  if (rc != LFD_OK) {
+    delete t;
+    return rc;
+  }
+  const PanelGeom& g = p->g;
+  const int64_t n_items = (int64_t)g.K * M;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = p->g_means2d.ensure((size_t)n_items * g.C * 8)) != LFD_OK ||
+      (rc = p->g_conic.ensure((size_t)n_items * 16)) != LFD_OK ||
+      (rc = p->g_color.ensure((size_t)n_items * 16)) != LFD_OK ||
+      (rc = p->g_opac.ensure((size_t)M * 4)) != LFD_OK) {
+    delete t;
+    return rc;
+  }
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->g_means2d.p, 0, (size_t)n_items * g.C * 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->g_conic.p, 0, (size_t)n_items * 16, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->g_color.p, 0, (size_t)n_items * 16, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->g_opac.p, 0, (size_t)M * 4, s);
+  BlendArgs ba;
+  ba.psi = p->psi;
+  ba.seg = p->seg;
+  ba.ranges = p->ranges.as<uint2>();
+  ba.list = p->pair_val[p->last_val_buf].as<uint32_t>();
+  ba.means2d = p->proj_means.as<float>();
+  ba.conic_opacity = p->proj_co.as<float>();
+  ba.color_tau = p->proj_ct.as<float>();
+  ba.M = M;
+  ba.bg[0] = p->opts.bg[0];
+  ba.bg[1] = p->opts.bg[1];
+  ba.bg[2] = p->opts.bg[2];
+  ba.out = nullptr;
+  ba.eval_counter = nullptr;
+  ba.max_segment = p->max_segment;
+  ba.V = p->V;
+  BlendGrads gr;
+  gr.grad_out = grad_rgb;
+  gr.grad_means2d = p->g_means2d.as<float>();
+  gr.grad_conic = p->g_conic.as<float>();
+  gr.grad_color = p->g_color.as<float>();
+  gr.grad_opac = p->g_opac.as<float>();
+  if (e == cudaSuccess) e = launch_blend_backward(g, ba, gr, s);
+  ProjectArgs a;
+  a.means = gs->means;
+  a.scales = gs->scales;
+  a.quats = gs->quats;
+  a.opac = gs->opacities;
+  a.sh = gs->sh;
+  a.M = M;
+  a.sh_degree = gs->sh_degree;
+  a.attr_dtype = gs->attr_dtype;
+  a.means2d = p->proj_means.as<float>();
+  a.conic_opacity = p->proj_co.as<float>();
+  a.color_tau = p->proj_ct.as<float>();
+  a.depth = p->proj_depth.as<float>();
+  ParamGrads out = {grad_means, grad_scales, grad_quats, grad_opacities, grad_sh};
+  if (e == cudaSuccess) e = launch_project_backward(g, *t, a, gr, out, s);
+  delete t;
+  if (e != cudaSuccess) return fail_cuda(e, "backward");
+  return LFD_OK;
+}
+
+int lfd_render_fullframe(lfd_plan* p, const lfd_gaussians* gs, const lfd_camera* cams,
+                         int32_t num_cams, float* out_rgb, void* stream, lfd_stats* stats) {
+  if (!p) return fail(LFD_ERR_INVALID, "NULL plan");
+  if (!p->ff_child) {
+    lfd_opts o = p->opts;
+    o.views_per_cluster = 1;
+    o.remap = 1;
+    int rc = lfd_plan_create(&p->panel, &o, &p->ff_child);
+    if (rc != LFD_OK) return rc;
+    p->ff_child->fullframe = true;
+  }
+  p->ff_child->flags = p->flags;
+  return lfd_render(p->ff_child, gs, cams, num_cams, out_rgb, stream, stats);
+}
+
 int lfd_render_host(lfd_plan* p, const lfd_gaussians* gh, const lfd_camera* cams, int32_t num_cams,
                     float* out_rgb_host, void* stream, lfd_stats* stats) {
   if (!p) return fail(LFD_ERR_INVALID, "NULL plan");
@@ -581,8 +710,9 @@ int lfd_render_host(lfd_plan* p, const lfd_gaussians* gh, const lfd_camera* cams
   const int64_t M = gh->count;
   if (M < 0 || gh->sh_degree < 0 || gh->sh_degree > 3) return fail(LFD_ERR_INVALID, "bad Gaussian set");
   const int ncoef = (gh->sh_degree + 1) * (gh->sh_degree + 1);
-  const size_t bytes[5] = {(size_t)M * 12, (size_t)M * 12, (size_t)M * 16, (size_t)M * 4,
-                           (size_t)M * ncoef * 12};
+  const size_t es = gh->attr_dtype == LFD_DTYPE_F32 ? 4 : 2;
+  const size_t bytes[5] = {(size_t)M * 12, (size_t)M * 3 * es, (size_t)M * 4 * es, (size_t)M * es,
+                           (size_t)M * ncoef * 3 * es};
   const void* src[5] = {gh->means, gh->scales, gh->quats, gh->opacities, gh->sh};
   cudaStream_t s = (cudaStream_t)stream;
   int rc;
@@ -597,10 +727,10 @@ int lfd_render_host(lfd_plan* p, const lfd_gaussians* gh, const lfd_camera* cams
   if ((rc = p->image.ensure(out_bytes)) != LFD_OK) return rc;
   lfd_gaussians gd = *gh;
   gd.means = p->host_in[0].as<float>();
-  gd.scales = p->host_in[1].as<float>();
-  gd.quats = p->host_in[2].as<float>();
-  gd.opacities = p->host_in[3].as<float>();
-  gd.sh = p->host_in[4].as<float>();
+  gd.scales = p->host_in[1].p;
+  gd.quats = p->host_in[2].p;
+  gd.opacities = p->host_in[3].p;
+  gd.sh = p->host_in[4].p;
   rc = lfd_render(p, &gd, cams, num_cams, p->image.as<float>(), stream, stats);
   if (rc != LFD_OK) return rc;
   LFD_CUDA(cudaMemcpyAsync(out_rgb_host, p->image.p, out_bytes, cudaMemcpyDeviceToHost, s));

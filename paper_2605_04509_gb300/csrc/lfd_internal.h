@@ -36,9 +36,11 @@ cudaError_t launch_remap(const PanelGeom& g, const uint8_t* V, uint32_t* psi,
 
 // ---- projection (project.cu) ----
 struct ProjectArgs {
-  const float *means, *scales, *quats, *opac, *sh;
+  const float* means;
+  const void *scales, *quats, *opac, *sh;  // element type given by attr_dtype
   int64_t M;
   int sh_degree;
+  int attr_dtype;  // LFD_DTYPE_*
   float* means2d;        // [K][M][C][2]
   float* conic_opacity;  // [K][M][4]
   float* color_tau;      // [K][M][4]
@@ -54,7 +56,7 @@ cudaError_t launch_item_keys(const PanelGeom& g, int64_t M, const float* depth,
                              cudaStream_t s);
 // Bytes per item of the optional union descriptors the count pass leaves for
 // the emit pass (nullptr: the emit pass recomputes the geometry).
-constexpr size_t kBinDescBytes = 64;
+constexpr size_t kBinDescBytes = 128;
 // tile count of the cluster union per item; items given by `order` (flat
 // k*M + i indices) or natural order when order == nullptr
 cudaError_t launch_bin_count(const PanelGeom& g, int64_t M, const float* means2d,
@@ -67,6 +69,16 @@ cudaError_t launch_bin_emit(const PanelGeom& g, int64_t M, const float* means2d,
                             const float* depth, const uint32_t* order, int64_t n_items,
                             const uint32_t* offsets, uint32_t* keys32, uint64_t* keys64,
                             uint32_t* vals, const void* desc, cudaStream_t s);
+// emission from descriptors indexed by item r (written by a natural-order
+// count pass); items visited in `order`, counts/offsets indexed by position
+cudaError_t launch_bin_emit_coop(const PanelGeom& g, int64_t M, const float* means2d,
+                                 const float* conic_opacity, const float* color_tau,
+                                 const float* depth, const uint32_t* order, int64_t n_items,
+                                 const uint32_t* counts, const uint32_t* offsets, uint32_t* keys32,
+                                 uint64_t* keys64, uint32_t* vals, const void* desc, cudaStream_t s);
+// dst[s] = src[idx[s]]
+cudaError_t launch_gather_u32(const uint32_t* src, const uint32_t* idx, int64_t n, uint32_t* dst,
+                              cudaStream_t s);
 cudaError_t launch_ranges(const PanelGeom& g, int64_t P, const uint32_t* keys32,
                           const uint64_t* keys64, uint2* ranges, cudaStream_t s);
 
@@ -100,8 +112,30 @@ struct BlendArgs {
   float* out;
   unsigned long long* eval_counter;  // non-null: [0] visited entries, [1] evaluated ones
   int max_segment;
+  const uint8_t* V;  // view index [H][W][3] (raster-order blend)
 };
 cudaError_t launch_blend(const PanelGeom& g, const BlendArgs& a, cudaStream_t s);
+// the same blend without the view-coherent remap (threads in raster order)
+cudaError_t launch_blend_raster(const PanelGeom& g, const BlendArgs& a, cudaStream_t s);
+// full-frame baseline: per-view pixel blend fused with the interlacing
+// (clusters are single views)
+cudaError_t launch_blend_fullframe(const PanelGeom& g, const BlendArgs& a, cudaStream_t s);
+
+// ---- backward (backward.cu) ----
+struct BlendGrads {
+  const float* grad_out;  // dL/dI [H][W][3]
+  float* grad_means2d;    // [K][M][C][2]
+  float* grad_conic;      // [K][M][4]: d/d(a, b, c) of the conic
+  float* grad_color;      // [K][M][4]
+  float* grad_opac;       // [M]
+};
+struct ParamGrads {
+  float *means, *scales, *quats, *opacities, *sh;
+};
+cudaError_t launch_blend_backward(const PanelGeom& g, const BlendArgs& a, const BlendGrads& gr,
+                                  cudaStream_t s);
+cudaError_t launch_project_backward(const PanelGeom& g, const CamTable& cams, const ProjectArgs& a,
+                                    const BlendGrads& gr, const ParamGrads& out, cudaStream_t s);
 
 // ---- read-only view of a plan and error reporting (lfd_api.cu) ----
 struct PlanView {
@@ -110,6 +144,8 @@ struct PlanView {
   const int32_t* seg;
   int max_segment;
   int sort_mode;
+  int remap;
+  const uint8_t* V;
   float bg[3];
   unsigned long long* h_small;  // pinned host words owned by the plan
 };

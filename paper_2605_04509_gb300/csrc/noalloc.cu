@@ -169,7 +169,11 @@ extern "C" int lfd_render_projected_noalloc(lfd_plan* plan, int64_t M, const flo
   ba.out = out_rgb;
   ba.eval_counter = nullptr;
   ba.max_segment = pv.max_segment;
-  NA_CUDA(launch_blend(g, ba, s));
+  ba.V = pv.V;
+  if (pv.remap)
+    NA_CUDA(launch_blend(g, ba, s));
+  else
+    NA_CUDA(launch_blend_raster(g, ba, s));
   if (stats) {
     stats->num_pairs = (int64_t)P;
     stats->num_visits = -1;

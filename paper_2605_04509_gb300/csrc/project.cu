@@ -4,10 +4,18 @@
 // view gives the 2D covariance (EWA splatting with the 3DGS Jacobian clamp and
 // +0.3 low-pass), its inverse (conic), the depth and the SH colour, and every
 // slot view of the cluster gives a 2D mean (Eq. 5). FP32 throughout.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "lfd_internal.h"
 
 namespace lfd {
 namespace {
+
+// Attribute storage types: FP32, FP16 or BF16, widened to FP32 on load.
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
 
 constexpr float kNear = 0.2f;
 constexpr float kDilation = 0.3f;
@@ -41,13 +49,19 @@ __device__ __forceinline__ float depth_rn(const float* c, float x, float y, floa
                    c[11]);
 }
 
+template <typename A>
 __global__ void __launch_bounds__(128) k_project(PanelGeom g, CamTable cams, ProjectArgs a) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.M) return;
+  const A* quats = reinterpret_cast<const A*>(a.quats);
+  const A* scales = reinterpret_cast<const A*>(a.scales);
+  const A* opac = reinterpret_cast<const A*>(a.opac);
+  const A* shs = reinterpret_cast<const A*>(a.sh);
   const float mx = a.means[3 * i], my = a.means[3 * i + 1], mz = a.means[3 * i + 2];
-  const float4 q4 = reinterpret_cast<const float4*>(a.quats)[i];
-  const float sx = a.scales[3 * i], sy = a.scales[3 * i + 1], sz = a.scales[3 * i + 2];
-  const float o = a.opac[i];
+  const float4 q4 = make_float4(to_f32(quats[4 * i]), to_f32(quats[4 * i + 1]), to_f32(quats[4 * i + 2]),
+                                to_f32(quats[4 * i + 3]));
+  const float sx = to_f32(scales[3 * i]), sy = to_f32(scales[3 * i + 1]), sz = to_f32(scales[3 * i + 2]);
+  const float o = to_f32(opac[i]);
 
   // Sigma3D = Rq diag(s^2) Rq^T
   const float qn = rsqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
@@ -72,7 +86,7 @@ __global__ void __launch_bounds__(128) k_project(PanelGeom g, CamTable cams, Pro
   for (int c = 0; c < 16; ++c) {
 #pragma unroll
     for (int u = 0; u < 3; ++u)
-      sh[c][u] = c < ncoef ? a.sh[((size_t)i * ncoef + c) * 3 + u] : 0.f;
+      sh[c][u] = c < ncoef ? to_f32(shs[((size_t)i * ncoef + c) * 3 + u]) : 0.f;
   }
   const bool opaque_enough = (double)o >= 1.0 / 255.0;
   const float tau_i = 2.f * logf(255.f * o);
@@ -180,7 +194,12 @@ cudaError_t launch_project(const PanelGeom& g, const CamTable& cams, const Proje
   if (a.M == 0) return cudaSuccess;
   const int threads = 128;
   const int64_t blocks = (a.M + threads - 1) / threads;
-  k_project<<<(unsigned)blocks, threads, 0, s>>>(g, cams, a);
+  if (a.attr_dtype == LFD_DTYPE_F16)
+    k_project<__half><<<(unsigned)blocks, threads, 0, s>>>(g, cams, a);
+  else if (a.attr_dtype == LFD_DTYPE_BF16)
+    k_project<__nv_bfloat16><<<(unsigned)blocks, threads, 0, s>>>(g, cams, a);
+  else
+    k_project<float><<<(unsigned)blocks, threads, 0, s>>>(g, cams, a);
   note_launches(1);
   return cudaGetLastError();
 }

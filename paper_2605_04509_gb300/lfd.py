@@ -44,10 +44,15 @@ class COpts(ct.Structure):
                 ("sort_mode", ct.c_int32), ("bg", ct.c_float * 3)]
 
 
+DTYPE_F32 = 0
+DTYPE_F16 = 1
+DTYPE_BF16 = 2
+
+
 class CGaussians(ct.Structure):
     _fields_ = [("means", ct.c_void_p), ("scales", ct.c_void_p), ("quats", ct.c_void_p),
                 ("opacities", ct.c_void_p), ("sh", ct.c_void_p), ("count", ct.c_int64),
-                ("sh_degree", ct.c_int32)]
+                ("sh_degree", ct.c_int32), ("attr_dtype", ct.c_int32)]
 
 
 class CCamera(ct.Structure):
@@ -102,6 +107,10 @@ def load() -> ct.CDLL:
                                               ct.POINTER(CStats)], ct.c_int),
             "lfd_render_host": ([_P, ct.POINTER(CGaussians), ct.POINTER(CCamera), ct.c_int32,
                                  _P, _P, ct.POINTER(CStats)], ct.c_int),
+            "lfd_render_backward": ([_P, ct.POINTER(CGaussians), ct.POINTER(CCamera), ct.c_int32,
+                                     _P, _P, _P, _P, _P, _P, _P], ct.c_int),
+            "lfd_render_fullframe": ([_P, ct.POINTER(CGaussians), ct.POINTER(CCamera), ct.c_int32,
+                                      _P, _P, ct.POINTER(CStats)], ct.c_int),
             "lfd_plan_copy_lists": ([_P, _P, _P, _P, ct.c_int64], ct.c_int),
             "lfd_get_stage_totals": ([_P, ct.POINTER(CStageTotals), ct.c_int32], ct.c_int),
             "lfd_kernel_launches": ([], ct.c_uint64),
@@ -162,19 +171,31 @@ def gaussians_struct(scene, host: bool = False) -> CGaussians:
     g.sh = ptr(scene["sh"])
     g.count = int(scene["means"].shape[0])
     g.sh_degree = num_sh_degree(tuple(scene["sh"].shape))
+    g.attr_dtype = _attr_dtype(scene["scales"])
+    for key in ("quats", "opacities", "sh"):
+        assert _attr_dtype(scene[key]) == g.attr_dtype, "attributes must share one storage type"
     return g
+
+
+def _attr_dtype(t) -> int:
+    name = str(t.dtype).split(".")[-1]
+    kinds = {"float32": DTYPE_F32, "float16": DTYPE_F16, "bfloat16": DTYPE_BF16}
+    if name not in kinds:
+        raise TypeError(f"unsupported attribute dtype {t.dtype}")
+    return kinds[name]
 
 
 class Plan:
     """A panel + options plan (lfd_plan_create); owns V, Psi and scratch."""
 
     def __init__(self, panel, tile: Tuple[int, int] = (16, 16), views_per_cluster: int = 8,
-                 sort_mode: int = SORT_DEPTH_FIRST, bg=(0.0, 0.0, 0.0)):
+                 sort_mode: int = SORT_DEPTH_FIRST, bg=(0.0, 0.0, 0.0), remap: bool = True):
         L = load()
         self.panel = panel
         cp = CPanel(panel.width, panel.height, panel.num_views, float(panel.tan_slant),
                     float(panel.pitch), float(panel.k_offset))
-        co = COpts(tile[0], tile[1], views_per_cluster, 1, sort_mode, (ct.c_float * 3)(*bg))
+        co = COpts(tile[0], tile[1], views_per_cluster, 1 if remap else 0, sort_mode,
+                   (ct.c_float * 3)(*bg))
         h = _P()
         _check(L.lfd_plan_create(ct.byref(cp), ct.byref(co), ct.byref(h)))
         self._h = h
@@ -271,6 +292,28 @@ class Plan:
                                  ct.byref(st)))
         return out, st.as_dict()
 
+    def backward(self, scene, cams: np.ndarray, grad_rgb, stream=None) -> Dict[str, object]:
+        """lfd_render_backward for the plan's last render(scene, cams)."""
+        import torch
+        grads = {k: torch.empty_like(scene[k]) for k in ("means", "scales", "quats", "opacities", "sh")}
+        g = gaussians_struct(scene)
+        carr, n = cameras_array(cams)
+        _check(load().lfd_render_backward(
+            self._h, ct.byref(g), carr, n, _dptr(grad_rgb.contiguous()), _dptr(grads["means"]),
+            _dptr(grads["scales"]), _dptr(grads["quats"]), _dptr(grads["opacities"]),
+            _dptr(grads["sh"]), _stream_ptr(stream)))
+        return grads
+
+    def render_fullframe(self, scene, cams: np.ndarray, out=None, stream=None) -> Tuple[object, Dict]:
+        """The full-frame baseline: every view rendered whole, then interlaced."""
+        out = self._image(out)
+        g = gaussians_struct(scene)
+        carr, n = cameras_array(cams)
+        st = CStats()
+        _check(load().lfd_render_fullframe(self._h, ct.byref(g), carr, n, _dptr(out),
+                                           _stream_ptr(stream), ct.byref(st)))
+        return out, st.as_dict()
+
     def render_host(self, scene_host, cams: np.ndarray, out_host, stream=None):
         """scene_host / out_host: contiguous CPU tensors (pinned for speed)."""
         g = gaussians_struct(scene_host, host=True)
@@ -300,9 +343,36 @@ def kernel_launches() -> int:
     return int(load().lfd_kernel_launches())
 
 
-def scene_to_device(scene: Dict[str, np.ndarray], device="cuda", dtype=None):
+def scene_to_device(scene: Dict[str, np.ndarray], device="cuda", attr_dtype=None):
+    """Scene arrays to device tensors; means stay FP32, the other attributes
+    are cast to attr_dtype (a torch dtype: float32, float16 or bfloat16)."""
     import torch
     out = {}
     for k, v in scene.items():
-        out[k] = torch.from_numpy(np.ascontiguousarray(v, dtype=np.float32)).to(device)
+        t = torch.from_numpy(np.ascontiguousarray(v, dtype=np.float32)).to(device)
+        if k != "means" and attr_dtype is not None:
+            t = t.to(attr_dtype).contiguous()
+        out[k] = t
     return out
+
+
+def render_autograd(plan: "Plan", cams: np.ndarray, means, scales, quats, opacities, sh):
+    """Differentiable interlaced render: forward through lfd_render, backward
+    through lfd_render_backward (a torch.autograd.Function)."""
+    import torch
+
+    class _Render(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, m, s, q, o, h):
+            scene = {"means": m.contiguous(), "scales": s.contiguous(), "quats": q.contiguous(),
+                     "opacities": o.contiguous(), "sh": h.contiguous()}
+            img, _ = plan.render(scene, cams)
+            ctx.scene = scene
+            return img
+
+        @staticmethod
+        def backward(ctx, grad_img):
+            g = plan.backward(ctx.scene, cams, grad_img.contiguous())
+            return g["means"], g["scales"], g["quats"], g["opacities"], g["sh"]
+
+    return _Render.apply(means, scales, quats, opacities, sh)
