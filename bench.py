@@ -37,7 +37,9 @@ METRIC = ("interlaced LFD frames/s and subpixels/s (4K panel, 45 views) vs plain
           "at <=1/255 err")
 WORKLOAD_TEXT = ("paper4k: 1M Gaussians (64-blob mixture, radius 10), 45 views over a 40 deg "
                  "cone at radius 30, 3840x2160 panel, slant 0.2 rad, pitch 5.3 subpixels, "
-                 "16x16 tiles, |V_k|=8 (K=6), SH degree 3, FP32")
+                 "|V_k|=8 (K=6), SH degree 3, FP32")
+# tile shapes the default run's autotuner tries (paper_2605_04509_gb300.autotune)
+AUTOTUNE_TILES = ((16, 16), (32, 16), (32, 8), (16, 8))
 # FP32 peak of the blend's pipe: 152 SMs x 128 FP32 lanes x 2070 MHz max SM clock
 SMS, FP32_LANES, SM_MAX_MHZ, MUFU_LANES = 152, 128, 2070.0, 16
 # algorithmic FP32 operations per visited (subpixel, Gaussian) evaluation:
@@ -56,7 +58,9 @@ def parse_args():
     ap.add_argument("--gaussians", type=int, default=0,
                     help="override the Gaussian count (profiling captures of a smaller case)")
     ap.add_argument("--views-per-cluster", type=int, default=8)
-    ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--tile", default="auto",
+                    help="WxH, or auto: the autotuner picks among " +
+                         ", ".join(f"{a}x{b}" for a, b in AUTOTUNE_TILES))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fullframe", action="store_true", help="skip the full-frame baseline")
@@ -173,10 +177,10 @@ def gpu_id_for(torch, index: int) -> str:
 # CPU oracle runs (bounded samples)
 # ---------------------------------------------------------------------------
 
-def blend_traffic_bytes():
-    """DRAM bytes (read + write) of one blend launch on this workload, from the
-    ncu capture summarised in profiles/k_blend_traffic.txt, or None when the
-    blend source has changed since that capture."""
+def blend_traffic_bytes(tile: str):
+    """DRAM bytes (read + write) of one blend launch on this workload and tile
+    shape, from the ncu capture summarised in profiles/k_blend_traffic.txt, or
+    None when the blend source or the tile differs from that capture."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "k_blend_traffic.txt")
     src = os.path.join(ROOT, "paper_2605_04509_gb300", "csrc", "blend.cu")
@@ -184,6 +188,8 @@ def blend_traffic_bytes():
         fields = dict(line.split(":", 1) for line in open(path) if ":" in line)
         digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
         if fields.get("blend_cu_sha256", "").strip() != digest:
+            return None
+        if fields.get("tile", "").strip() != tile:
             return None
         return int(fields["dram_bytes_per_launch"].strip())
     except (OSError, KeyError, ValueError):
@@ -217,7 +223,8 @@ def run_reference(args):
     import oracle
     from paper_2605_04509_gb300 import synth
     w = synth.WORKLOADS[args.workload]
-    tile = tuple(int(v) for v in args.tile.split("x"))
+    # the oracle's binned blend gives the same image for any tile shape
+    tile = (16, 16) if args.tile == "auto" else tuple(int(v) for v in args.tile.split("x"))
     scene = synth.scene_for(w)
     cams = synth.arc_cameras(w.rig, w.panel.width, w.panel.height)
     V = oracle.view_index(w.panel)
@@ -247,7 +254,7 @@ def run_reference(args):
         "ms_per_step": 1000.0 * t_total / max(args.steps, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_TEXT, "views_per_cluster": args.views_per_cluster,
-                   "tile": args.tile},
+                   "tile": f"{tile[0]}x{tile[1]} (oracle binning)"},
         "subpixels_per_s": sub_total / t_total,
         "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cores, "kind": "oracle",
                          "sample": "per step: FP64 projection of all 1M Gaussians + binned FP64 "
@@ -274,10 +281,27 @@ def run_ours(args):
 
     w = synth.WORKLOADS[args.workload]
     C = args.views_per_cluster
-    tile = tuple(int(v) for v in args.tile.split("x"))
     scene = synth.scene_for(w, args.gaussians or None)
     cams = synth.arc_cameras(w.rig, w.panel.width, w.panel.height)
     dscene = lfd.scene_to_device(scene, device)
+    autotune = None
+    if args.tile == "auto":
+        # untimed: two frames per candidate tile shape on this scene; rank 0's
+        # choice is used by every rank
+        from paper_2605_04509_gb300 import autotune as at
+        res = at.tune(w.panel, dscene, cams, views_per_cluster=C, tiles=AUTOTUNE_TILES,
+                      subpixels_per_thread=(0,), frames=2, warmup=1)
+        choice = torch.tensor(res["best"]["tile"], dtype=torch.int64, device=device)
+        if world > 1:
+            import torch.distributed as dist
+            dist.broadcast(choice, 0)
+        tile = (int(choice[0]), int(choice[1]))
+        autotune = {"chosen": f"{tile[0]}x{tile[1]}",
+                    "ms_per_frame": {f"{r['tile'][0]}x{r['tile'][1]}": round(r["ms"], 3)
+                                     for r in res["results"]}}
+    else:
+        tile = tuple(int(v) for v in args.tile.split("x"))
+    tile_text = f"{tile[0]}x{tile[1]}"
     plan = lfd.Plan(w.panel, tile=tile, views_per_cluster=C)
     out = torch.empty((w.panel.height, w.panel.width, 3), dtype=torch.float32, device=device)
     stream = torch.cuda.current_stream(device)
@@ -320,8 +344,8 @@ def run_ours(args):
     achieved = E * OPS_PER_EVAL / (blend_ms * 1e-3) / 1e12
     peak = SMS * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12
     ex2_frac = E / (blend_ms * 1e-3) / (SMS * MUFU_LANES * SM_MAX_MHZ * 1e6)
-    traffic = blend_traffic_bytes() if (args.workload == "paper4k" and not args.gaussians
-                                        and C == 8 and args.tile == "16x16") else None
+    traffic = blend_traffic_bytes(tile_text) if (args.workload == "paper4k" and not args.gaussians
+                                                 and C == 8) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOP/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": "k_blend",
                 "units": f"E = {E} visited (subpixel, Gaussian) evaluations per launch x "
@@ -333,7 +357,9 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_TEXT, "views_per_cluster": C, "tile": args.tile,
+        "config": {"workload": WORKLOAD_TEXT, "views_per_cluster": C, "tile": tile_text,
+                   "tile_choice": ("autotuned (untimed, before the warm-up)" if autotune
+                                   else "fixed by --tile"),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2: 236 MB of Gaussians, ~0.6 GB of projected "
                          "attributes and several hundred MB of pairs per frame"},
@@ -341,6 +367,7 @@ def run_ours(args):
         "pairs": P, "evals": E,
         "stages_ms": {k: stages[k] / n_frames_staged for k in ("ms_project", "ms_keygen", "ms_sort", "ms_blend")},
         "roofline": roofline,
+        "autotune": autotune,
         "gpu_launches": int(launches),
         "clocks": clocks,
     }

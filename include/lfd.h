@@ -74,6 +74,9 @@ extern "C" {
 #define LFD_ERR_CAPACITY (-3) /* pair count or key width beyond the limits   */
 #define LFD_ERR_CUDA (-4)     /* a CUDA call failed; see lfd_last_error()    */
 #define LFD_ERR_STATE (-5)    /* the requested data does not exist (yet)     */
+#define LFD_ERR_TIMEOUT (-6)  /* a bounded device wait gave up (the sort's
+                               * bulk-copy waits); reported at the plan's
+                               * next read-back, the frame it hit is wrong  */
 
 /* Key-generation and sort strategy. Both produce the identical sorted list
  * and range table.
@@ -103,13 +106,18 @@ typedef struct {
  * [1, 32] (C = 1: no attribute reuse); remap 1 = view-coherent remapping
  * (Sec. 4.3), 0 = subpixels in raster order, each thread walking its own list
  * (the ablation "w/o remap"; same image); sort_mode one of LFD_SORT_*; bg is
- * the background colour added as T * bg. */
+ * the background colour added as T * bg. subpixels_per_thread (0 = automatic,
+ * else 1, 2, 4 or 8) sets how many subpixels of a (tile, cluster) run one
+ * blend thread owns, and with it the blend's staging depth (list entries
+ * staged in shared memory per batch = threads per block); it changes speed
+ * only, never the image. */
 typedef struct {
   int32_t tile_w, tile_h;
   int32_t views_per_cluster;
   int32_t remap;
   int32_t sort_mode;
   float bg[3];
+  int32_t subpixels_per_thread;
 } lfd_opts;
 
 /* Storage type of the Gaussians' scales, rotations, opacities and SH
@@ -272,6 +280,66 @@ LFD_API int lfd_render_projected_noalloc(lfd_plan *plan, int64_t M, const float 
                                          const float *depth, float *out_rgb, void *stream,
                                          lfd_stats *stats);
 
+/* ---- Capacity mode: frames without host read-back (CUDA graphs) ----
+ * The paper renders with a host-side pair count (Alg. 1 sizes the key
+ * buffers from the offsets scan); these calls have no counterpart there.
+ *
+ * lfd_plan_reserve preallocates every per-frame buffer of the plan for up to
+ * max_gaussians Gaussians and max_pairs Gaussian-(tile, cluster) pairs and
+ * switches the plan to capacity mode (max_pairs = 0 switches it back).
+ * In capacity mode lfd_render / lfd_render_projected never allocate, never
+ * synchronise and never read anything back: the pair count P stays on the
+ * device, and every kernel after the offsets scan reads it there. A frame
+ * with P > max_pairs writes no pairs and leaves out_rgb untouched; it is
+ * reported (LFD_ERR_CAPACITY) by the next lfd_plan_status. More Gaussians
+ * than reserved fail at once with LFD_ERR_CAPACITY. Stage timing and
+ * evaluation counting are off in this mode and stats->num_pairs is -1.
+ * Such frames can be captured into a CUDA graph once the plan has rendered
+ * one frame outside the capture (which sets kernel attributes); a replay
+ * renders the Gaussians and cameras of the captured call (the cameras are
+ * baked into the graph; the Gaussians are read from the captured device
+ * pointers, so new values in those buffers are rendered).
+ * Synchronous; frees and reallocates the plan's buffers when they grow.
+ *
+ * lfd_plan_status synchronises the device and returns LFD_ERR_CAPACITY if a
+ * frame since the previous call overflowed, LFD_ERR_TIMEOUT if a bounded
+ * wait gave up, else LFD_OK; *pairs (may be NULL) receives the last frame's
+ * pair count, also when it overflowed (reserve that much and render again).
+ * The flags are cleared by the call. */
+LFD_API int lfd_plan_reserve(lfd_plan *plan, int64_t max_gaussians, int64_t max_pairs);
+LFD_API int lfd_plan_status(lfd_plan *plan, int64_t *pairs);
+
+/* ---- Batched rendering of several scenes per frame ----
+ * Not in the paper (it renders one panel per frame): the serving form of
+ * Alg. 1 for up to 16 scenes, each with its own plan (panel, tiles,
+ * clusters; several scenes may share one plan), Gaussians, cameras and
+ * image. Projection and per-item binning run per scene; the item sort, the
+ * offsets scan, the pair sort (Eq. 11 keys over a global tile numbering:
+ * scene s owns the tiles after those of scenes 0..s-1) and the range search
+ * run once for all scenes, and one persistent blend kernel takes the
+ * (scene, cluster, tile) runs from a work counter. Each scene's image equals
+ * the single-scene lfd_render of that scene bit for bit.
+ * Plans must use LFD_SORT_DEPTH_FIRST, remap = 1 and the same
+ * subpixels_per_thread; the global tile and cluster bits must fit 32.
+ * The batch keeps pointers to the plans (their V, Psi and run tables): the
+ * plans must outlive it. A batch always runs in capacity mode:
+ * lfd_batch_reserve (per-scene Gaussian capacities [num_scenes], total pair
+ * capacity) must precede rendering, and lfd_batch_render neither allocates
+ * nor synchronises nor reads back, so it can be captured into a CUDA graph
+ * (after one uncaptured frame). scenes: num_scenes device Gaussian sets;
+ * cams: num_scenes host arrays, array s holding the num_views cameras of
+ * scene s's panel; out_rgb: num_scenes device images [H_s][W_s][3].
+ * Overflow and wait errors are reported by lfd_batch_status exactly as
+ * lfd_plan_status reports them (an overflowing frame leaves every image
+ * untouched). */
+typedef struct lfd_batch lfd_batch;
+LFD_API int lfd_batch_create(lfd_plan *const *plans, int32_t num_scenes, lfd_batch **out);
+LFD_API void lfd_batch_destroy(lfd_batch *batch);
+LFD_API int lfd_batch_reserve(lfd_batch *batch, const int64_t *max_gaussians, int64_t max_pairs);
+LFD_API int lfd_batch_render(lfd_batch *batch, const lfd_gaussians *scenes,
+                             const lfd_camera *const *cams, float *const *out_rgb, void *stream);
+LFD_API int lfd_batch_status(lfd_batch *batch, int64_t *pairs);
+
 /* Stage times accumulated over frames rendered with LFD_FLAG_STAGE_TIMING,
  * measured with CUDA events on each frame's stream and folded in without
  * extra synchronisation (a frame's events are read at the next frame's
@@ -282,6 +350,15 @@ typedef struct {
 } lfd_stage_times;
 
 LFD_API int lfd_get_stage_totals(lfd_plan *plan, lfd_stage_times *out, int32_t reset);
+
+/* Self-test of the library's bounded device waits (no counterpart in the
+ * paper): a kernel waits on an mbarrier phase that nothing completes, the
+ * kind of wait the sort's pipelined scatter makes on its bulk copies.
+ * Returns LFD_ERR_TIMEOUT when the wait gave up after its bound and the
+ * kernel finished (the expected outcome, after about a quarter of a second),
+ * LFD_OK if it did not, or LFD_ERR_CUDA. Synchronises the stream; allocates
+ * and frees a 4-byte flag. */
+LFD_API int lfd_selftest_wait_timeout(void *stream);
 
 /* Number of CUDA kernels this library has launched in the process so far. */
 LFD_API uint64_t lfd_kernel_launches(void);

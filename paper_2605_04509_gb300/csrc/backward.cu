@@ -16,12 +16,6 @@ constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTMin = 1e-4f;
 
-__device__ __forceinline__ float ex2_approx(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
 // ---------------------------------------------------------------------------
 // blend backward: one CTA per (tile, cluster) run of Psi, one subpixel per
 // thread; the list is staged in shared memory batch by batch, first front to
@@ -83,8 +77,8 @@ __global__ void __launch_bounds__(256) k_blend_backward(PanelGeom g, BlendArgs a
     const float4 co = s_co[gi];
     const float2 mu = s_mean[slot * NB + gi];
     const float dx = px - mu.x, dy = py - mu.y;
-    const float power = (-0.5f * kLog2e * co.x) * dx * dx + (-0.5f * kLog2e * co.z) * dy * dy +
-                        (-kLog2e * co.y) * dx * dy;
+    // the forward blend's pre-scaled conic and order of operations
+    const float power = quad_power(-0.5f * kLog2e * co.x, -kLog2e * co.y, -0.5f * kLog2e * co.z, dx, dy);
     if (power > 0.f) return 0.f;
     const float v = co.w * ex2_approx(power);
     if (!(v >= kAlphaMin)) return 0.f;

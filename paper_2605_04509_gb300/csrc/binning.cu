@@ -189,7 +189,7 @@ __global__ void k_item_keys(PanelGeom g, int64_t M, const float* __restrict__ de
   const uint64_t k = (uint64_t)(r / M);
   const float tau = color_tau[r].w;
   const uint32_t d = tau >= 0.f ? __float_as_uint(depth[r]) : 0xffffffffu;
-  keys[r] = (k << 32) | d;
+  keys[r] = ((k + (uint64_t)g.cluster_base) << 32) | d;
   vals[r] = (uint32_t)r;
 }
 
@@ -238,25 +238,54 @@ constexpr int kBinWarps = 4;
 // items; their tile rows are dealt out to the lanes as separate work units,
 // so a large Gaussian does not hold up its warp. A unit unites the cluster's
 // views over one tile row. Items whose union is wider than 64 tile columns
-// are walked by their own lane.
+// are walked by their own lane. Each item's per-view boxes (bin_view) are
+// computed once by its own lane and kept in shared memory for the units.
+struct BoxS {
+  float mx, my, bx0, bx1;
+  int y0, y1;  // y0 > y1: the view does not see the Gaussian
+};
+
 __global__ void __launch_bounds__(32 * kBinWarps)
     k_bin_count(PanelGeom g, int64_t M, const float2* __restrict__ means2d,
                 const float4* __restrict__ conic_opacity, const float4* __restrict__ color_tau,
                 const uint32_t* __restrict__ order, int64_t n_items, uint32_t* __restrict__ counts,
                 BinDesc* __restrict__ desc) {
   __shared__ uint32_t s_n[kBinWarps][32];
+  extern __shared__ BoxS s_box[];  // [kBinWarps][32][C]
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool in = s < n_items;
   uint32_t r = 0;
   BinQ q = {};
   bool ok = false;
-  int ty0 = 0, ty1 = -1, c0 = 0, c1 = -1;
+  int ty0 = INT_MAX, ty1 = -1, c0 = INT_MAX, c1 = -1;
+  BoxS* my_box = s_box + (size_t)(warp * 32 + lane) * g.C;
   if (in) {
     r = order ? order[s] : (uint32_t)s;
     const float4 co = conic_opacity[r];
     ok = bin_prep(co.x, co.y, co.z, color_tau[r].w, q);
-    if (ok) bin_extent(g, q, means2d + (size_t)r * g.C, ty0, ty1, c0, c1);
+  }
+  if (ok) {
+    // bin_extent, keeping each view's box
+    const float2* mr = means2d + (size_t)r * g.C;
+    for (int l = 0; l < g.C; ++l) {
+      const float2 m = mr[l];
+      BinV v;
+      bin_view(q, m.x, m.y, g.W, g.H, v);
+      BoxS b;
+      b.mx = v.mx;
+      b.my = v.my;
+      b.bx0 = v.bx0;
+      b.bx1 = v.bx1;
+      b.y0 = v.valid ? v.y0 : 1;
+      b.y1 = v.valid ? v.y1 : 0;
+      my_box[l] = b;
+      if (!v.valid) continue;
+      ty0 = min(ty0, v.y0 / g.TH);
+      ty1 = max(ty1, v.y1 / g.TH);
+      c0 = min(c0, (int)v.bx0 / g.TW);
+      c1 = max(c1, (int)v.bx1 / g.TW);
+    }
   }
   const int rows = ok && ty1 >= ty0 ? ty1 - ty0 + 1 : 0;
   const bool wide = rows > 0 && c1 - c0 >= 64;
@@ -275,18 +304,23 @@ __global__ void __launch_bounds__(32 * kBinWarps)
     const int j = unit_owner(ubase, u);
     const int rr = u - __shfl_sync(0xffffffffu, ubase, j);
     const BinQ qj = shfl_q(q, j);
-    const uint32_t rj = __shfl_sync(0xffffffffu, r, j);
     const int ty0j = __shfl_sync(0xffffffffu, ty0, j);
     const int c0j = __shfl_sync(0xffffffffu, c0, j);
     const bool fitsj = __shfl_sync(0xffffffffu, fits, j);
     if (u < U) {
-      const float2* mj = means2d + (size_t)rj * g.C;
+      const BoxS* bj = s_box + (size_t)(warp * 32 + j) * g.C;
       const int ty = ty0j + rr;
       unsigned long long mask = 0ull;
       for (int l = 0; l < g.C; ++l) {
-        const float2 m = mj[l];
+        const BoxS bx = bj[l];
         BinV v;
-        bin_view(qj, m.x, m.y, g.W, g.H, v);
+        v.mx = bx.mx;
+        v.my = bx.my;
+        v.bx0 = bx.bx0;
+        v.bx1 = bx.bx1;
+        v.y0 = bx.y0;
+        v.y1 = bx.y1;
+        v.valid = bx.y0 <= bx.y1;
         int a, bb;
         if (!bin_row(qj, v, ty, g.TW, g.TH, a, bb)) continue;
         const int len = bb - a + 1;
@@ -386,13 +420,20 @@ __global__ void __launch_bounds__(32 * kEmitWarps)
                       const float* __restrict__ depth, const uint32_t* __restrict__ order,
                       int64_t n_items, const uint32_t* __restrict__ counts,
                       const uint32_t* __restrict__ offsets, KeyT* __restrict__ keys,
-                      uint32_t* __restrict__ vals, const BinDesc* __restrict__ desc) {
+                      uint32_t* __restrict__ vals, const BinDesc* __restrict__ desc,
+                      const unsigned long long* __restrict__ P_dev, unsigned long long P_cap,
+                      uint32_t* __restrict__ err) {
   constexpr int CAP = EmitCap<KeyT>::value;
   constexpr bool kWide = sizeof(KeyT) == 8;
   __shared__ KeyT s_key[kEmitWarps][CAP];
   __shared__ uint32_t s_val[kEmitWarps][CAP];
+  __shared__ __align__(16) unsigned long long s_desc[kEmitWarps][32][kDescRows + 1];
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (P_dev && *P_dev > P_cap) {  // more pairs than the buffers hold: write nothing
+    if (s == 0) atomicOr(err, 2u);
+    return;
+  }
   const bool in = s < n_items;
   uint32_t r = 0, n = 0, pos = 0;
   unsigned long long h = 0ull;
@@ -424,7 +465,8 @@ __global__ void __launch_bounds__(32 * kEmitWarps)
     BinQ q;
     if (bin_prep(co.x, co.y, co.z, color_tau[r].w, q))
       bin_union(g, q, means2d + (size_t)r * g.C, [&](int t) {
-        kdst[p] = kWide ? (KeyT)(((uint64_t)t << shift) | lo) : (KeyT)(((uint32_t)t << shift) | k);
+        const uint32_t tg = (uint32_t)(t + g.tile_base);
+        kdst[p] = kWide ? (KeyT)(((uint64_t)tg << shift) | lo) : (KeyT)((tg << shift) | k);
         vdst[p] = i;
         ++p;
       });
@@ -433,6 +475,19 @@ __global__ void __launch_bounds__(32 * kEmitWarps)
   const int units = (in && n && !redo) ? (int)((h >> 32) & 0xffull) : 0;
   int U;
   const int ubase = warp_exclusive(units, lane, &U);
+  // the row masks of the warp's items, fetched into shared memory with
+  // independent 16-byte loads (8 lanes per item, only the rows in use)
+  for (int it = 0; it < 8; ++it) {
+    const int j = it * 4 + (lane >> 3);
+    const int part = lane & 7;  // 16-byte part: words 2 part, 2 part + 1
+    const uint32_t rj = __shfl_sync(0xffffffffu, r, j);
+    const int uj = __shfl_sync(0xffffffffu, units, j);
+    if (uj > 0 && 2 * part <= uj) {
+      const uint4 w = reinterpret_cast<const uint4*>(desc + rj)[part];
+      reinterpret_cast<uint4*>(&s_desc[warp][j][0])[part] = w;
+    }
+  }
+  __syncwarp();
   for (int b = 0; b < U; b += 32) {
     const int u = b + lane;
     const int j = unit_owner(ubase, u);
@@ -448,12 +503,13 @@ __global__ void __launch_bounds__(32 * kEmitWarps)
       const uint32_t i = (uint32_t)(rj - (uint64_t)k * M);
       const uint64_t lo = kWide ? (((uint64_t)k << 32) | __float_as_uint(depth[rj])) : 0ull;
       uint32_t p = pj - shift_out;
-      for (int x = 0; x < rr; ++x) p += (uint32_t)__popcll(desc[rj].mask[x]);
-      unsigned long long mask = desc[rj].mask[rr];
+      const unsigned long long* dm = &s_desc[warp][j][1];
+      for (int x = 0; x < rr; ++x) p += (uint32_t)__popcll(dm[x]);
+      unsigned long long mask = dm[rr];
       while (mask) {
         const int bit = __ffsll((long long)mask) - 1;
         mask &= mask - 1ull;
-        const uint32_t t = (uint32_t)((ty0 + rr) * g.TX + c0 + bit);
+        const uint32_t t = (uint32_t)((ty0 + rr) * g.TX + c0 + bit + g.tile_base);
         kdst[p] = kWide ? (KeyT)(((uint64_t)t << shift) | lo) : (KeyT)((t << shift) | k);
         vdst[p] = i;
         ++p;
@@ -475,19 +531,34 @@ __global__ void k_gather_u32(const uint32_t* __restrict__ src, const uint32_t* _
   if (s < n) dst[s] = src[idx[s]];
 }
 
-__global__ void k_ranges(PanelGeom g, int64_t P, const uint32_t* __restrict__ keys32,
-                         const uint64_t* __restrict__ keys64, uint2* __restrict__ ranges) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= P) return;
-  auto tk_at = [&](int64_t q) -> uint32_t {
-    return keys64 ? (uint32_t)(keys64[q] >> 32) : keys32[q];
+// One thread per (tile, cluster) run: lower bounds of its key and of the
+// next key in the sorted pairs (the keys' upper 32 bits in Eq. 11 mode).
+__global__ void k_ranges(PanelGeom g, int64_t P_cap, const unsigned long long* __restrict__ P_dev,
+                         const uint32_t* __restrict__ keys32, const uint64_t* __restrict__ keys64,
+                         uint2* __restrict__ ranges) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (int64_t)g.T * g.K) return;
+  int64_t P = P_cap;
+  if (P_dev && *P_dev < (unsigned long long)P_cap) P = (int64_t)*P_dev;
+  const int t = (int)(q / g.K), k = (int)(q - (int64_t)t * g.K);
+  const uint32_t target = ((uint32_t)t << g.bit_k) | (uint32_t)k;
+  auto tk_at = [&](int64_t i) -> uint32_t {
+    return keys64 ? (uint32_t)(keys64[i] >> 32) : keys32[i];
   };
-  const uint32_t tk = tk_at(p);
-  const uint32_t t = tk >> g.bit_k;
-  const uint32_t k = tk & ((1u << g.bit_k) - 1u);
-  uint2* r = ranges + (size_t)t * g.K + k;
-  if (p == 0 || tk_at(p - 1) != tk) r->x = (uint32_t)p;
-  if (p == P - 1 || tk_at(p + 1) != tk) r->y = (uint32_t)(p + 1);
+  int64_t lo = 0, hi = P;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (tk_at(mid) < target) lo = mid + 1;
+    else hi = mid;
+  }
+  int64_t lo2 = lo;
+  hi = P;
+  while (lo2 < hi) {
+    const int64_t mid = (lo2 + hi) >> 1;
+    if (tk_at(mid) <= target) lo2 = mid + 1;
+    else hi = mid;
+  }
+  ranges[q] = lo2 > lo ? make_uint2((uint32_t)lo, (uint32_t)lo2) : make_uint2(0u, 0u);
 }
 
 inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
@@ -511,7 +582,13 @@ cudaError_t launch_bin_count(const PanelGeom& g, int64_t M, const float* means2d
                              const uint32_t* order, int64_t n_items, uint32_t* counts, void* desc,
                              cudaStream_t s) {
   if (n_items == 0) return cudaSuccess;
-  k_bin_count<<<blocks_for(n_items, 32 * kBinWarps), 32 * kBinWarps, 0, s>>>(
+  const size_t smem = (size_t)kBinWarps * 32 * g.C * sizeof(BoxS);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_bin_count<<<blocks_for(n_items, 32 * kBinWarps), 32 * kBinWarps, smem, s>>>(
       g, M, reinterpret_cast<const float2*>(means2d),
       reinterpret_cast<const float4*>(conic_opacity), reinterpret_cast<const float4*>(color_tau),
       order, n_items, counts, reinterpret_cast<BinDesc*>(desc));
@@ -537,7 +614,9 @@ cudaError_t launch_bin_emit_coop(const PanelGeom& g, int64_t M, const float* mea
                                  const float* conic_opacity, const float* color_tau,
                                  const float* depth, const uint32_t* order, int64_t n_items,
                                  const uint32_t* counts, const uint32_t* offsets, uint32_t* keys32,
-                                 uint64_t* keys64, uint32_t* vals, const void* desc, cudaStream_t s) {
+                                 uint64_t* keys64, uint32_t* vals, const void* desc,
+                                 const unsigned long long* P_dev, unsigned long long P_cap,
+                                 uint32_t* err, cudaStream_t s) {
   if (n_items == 0) return cudaSuccess;
   const unsigned blocks = blocks_for(n_items, 32 * kEmitWarps);
   if (keys64)
@@ -545,13 +624,13 @@ cudaError_t launch_bin_emit_coop(const PanelGeom& g, int64_t M, const float* mea
         g, M, reinterpret_cast<const float2*>(means2d),
         reinterpret_cast<const float4*>(conic_opacity), reinterpret_cast<const float4*>(color_tau),
         depth, order, n_items, counts, offsets, keys64, vals,
-        reinterpret_cast<const BinDesc*>(desc));
+        reinterpret_cast<const BinDesc*>(desc), P_dev, P_cap, err);
   else
     k_bin_emit_staged<uint32_t><<<blocks, 32 * kEmitWarps, 0, s>>>(
         g, M, reinterpret_cast<const float2*>(means2d),
         reinterpret_cast<const float4*>(conic_opacity), reinterpret_cast<const float4*>(color_tau),
         depth, order, n_items, counts, offsets, keys32, vals,
-        reinterpret_cast<const BinDesc*>(desc));
+        reinterpret_cast<const BinDesc*>(desc), P_dev, P_cap, err);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -564,10 +643,12 @@ cudaError_t launch_gather_u32(const uint32_t* src, const uint32_t* idx, int64_t 
   return cudaGetLastError();
 }
 
-cudaError_t launch_ranges(const PanelGeom& g, int64_t P, const uint32_t* keys32,
-                          const uint64_t* keys64, uint2* ranges, cudaStream_t s) {
-  if (P == 0) return cudaSuccess;
-  k_ranges<<<blocks_for(P, 256), 256, 0, s>>>(g, P, keys32, keys64, ranges);
+cudaError_t launch_ranges(const PanelGeom& g, int64_t P, const unsigned long long* P_dev,
+                          const uint32_t* keys32, const uint64_t* keys64, uint2* ranges,
+                          cudaStream_t s) {
+  const int64_t runs = (int64_t)g.T * g.K;
+  if (runs == 0) return cudaSuccess;
+  k_ranges<<<blocks_for(runs, 256), 256, 0, s>>>(g, P, P_dev, keys32, keys64, ranges);
   note_launches(1);
   return cudaGetLastError();
 }

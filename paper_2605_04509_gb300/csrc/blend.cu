@@ -19,9 +19,12 @@
 // staged view-major ([view][entry]) so that staging stores and per-view reads
 // do not collide in shared-memory banks. An entry whose exponent lies below
 // log2(1 / (255 o)) (less a 1e-4 margin) is skipped before the exp2: it cannot
-// reach alpha >= 1/255. Each thread owns two subpixels of the run. Grid order
-// is cluster-major so that one cluster's attributes stay resident in L2 while
-// its tiles are blended.
+// reach alpha >= 1/255. A thread owns R subpixels of the run (R = 2 unless
+// the plan sets another staging depth) and takes its view's entries two at a
+// time: the loads, quadratic forms and exponentials of the pair are
+// independent, and the transmittance is then updated in list order. Grid
+// order is cluster-major so that one cluster's attributes stay resident in L2
+// while its tiles are blended.
 #include "lfd_internal.h"
 
 namespace lfd {
@@ -32,30 +35,23 @@ constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTMin = 1e-4f;
 
-__device__ __forceinline__ float ex2_approx(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
+// Blend of one (tile t, cluster k) run whose list is [rg.x, rg.y). Called by
+// every thread of the block (it synchronises the block); returns uniformly.
 template <int R, bool COUNT>
-__global__ void __launch_bounds__(256) k_blend(PanelGeom g, BlendArgs a) {
-  extern __shared__ float4 smem[];
+__device__ __forceinline__ void blend_run(const PanelGeom& g, const BlendArgs& a, int k, int t,
+                                          uint2 rg, float4* smem) {
   const int NB = blockDim.x;  // a multiple of 32
   const int NW = NB >> 5;
   const int C = g.C;
-  float4* s_co = smem;        // conic * (-log2(e) / 2, -log2(e), -log2(e) / 2), opacity
-  float4* s_col = smem + NB;  // colour
-  float2* s_mean = reinterpret_cast<float2*>(smem + 2 * NB);        // [C][NB]
+  float4* s_co = smem;  // conic * (-log2(e) / 2, -log2(e), -log2(e) / 2), skip threshold
+  float2* s_oc = reinterpret_cast<float2*>(smem + NB);              // [3][NB] (opacity, colour u)
+  float2* s_mean = reinterpret_cast<float2*>(smem + 2 * NB) + NB;   // [C][NB]
   uint16_t* s_idx = reinterpret_cast<uint16_t*>(s_mean + NB * C);   // [C][NB]
   int* s_cnt = reinterpret_cast<int*>(s_idx + ((C * NB + 1) & ~1));  // [C][NW + 1]
 
-  const int k = blockIdx.x / g.T;
-  const int t = blockIdx.x - k * g.T;
   const int s0 = a.seg[(size_t)t * (g.K + 1) + k];
   const int n = a.seg[(size_t)t * (g.K + 1) + k + 1] - s0;
   if (n <= 0) return;
-  const uint2 rg = a.ranges[(size_t)t * g.K + k];
   const int tx = t % g.TX, ty = t / g.TX;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
@@ -113,9 +109,12 @@ __global__ void __launch_bounds__(256) k_blend(PanelGeom g, BlendArgs a) {
       const size_t rec = (size_t)k * a.M + gid;
       const float4 co = reinterpret_cast<const float4*>(a.conic_opacity)[rec];
       const float4 ct = reinterpret_cast<const float4*>(a.color_tau)[rec];
-      s_co[threadIdx.x] = make_float4(-0.5f * kLog2e * co.x, -kLog2e * co.y, -0.5f * kLog2e * co.z, co.w);
       // w: log2 of the opacity ratio at which alpha reaches 1/255 (skip below)
-      s_col[threadIdx.x] = make_float4(ct.x, ct.y, ct.z, -log2f(255.f * co.w) - 1e-4f);
+      s_co[threadIdx.x] = make_float4(-0.5f * kLog2e * co.x, -kLog2e * co.y, -0.5f * kLog2e * co.z,
+                                      -log2f(255.f * co.w) - 1e-4f);
+      s_oc[threadIdx.x] = make_float2(co.w, ct.x);
+      s_oc[NB + threadIdx.x] = make_float2(co.w, ct.y);
+      s_oc[2 * NB + threadIdx.x] = make_float2(co.w, ct.z);
       const float det = co.x * co.z - co.y * co.y;
       const float hx = sqrtf(fmaxf(ct.w * co.z / det, 0.f));
       const float hy = sqrtf(fmaxf(ct.w * co.x / det, 0.f));
@@ -156,30 +155,65 @@ __global__ void __launch_bounds__(256) k_blend(PanelGeom g, BlendArgs a) {
       if (!act[m]) continue;
       const uint16_t* idx = s_idx + slot[m] * NB;
       const int cnt = s_cnt[slot[m] * (NW + 1) + NW];
-      int stop = -1;
-      for (int q = 0; q < cnt; ++q) {
-        const int gi = idx[q];
-        if (COUNT) ++n_eval;
-        const float4 co = s_co[gi];
-        const float4 cl = s_col[gi];
-        const float2 mu = s_mean[slot[m] * NB + gi];
-        const float dx = px[m] - mu.x;
-        const float dy = py[m] - mu.y;
-        const float power = co.x * dx * dx + co.z * dy * dy + co.y * dx * dy;
-        if (power > 0.f || power < cl.w) continue;
-        const float v = co.w * ex2_approx(power);
-        if (!(v >= kAlphaMin)) continue;
+      int stop = -1, stop_q = -1;
+      const float2* mrow = s_mean + slot[m] * NB;
+      const float2* orow = s_oc + ch[m] * NB;
+      // Entries are taken two at a time: their loads, quadratic forms and
+      // exponentials are independent; the transmittance update stays in
+      // list order, one entry after the other.
+      auto apply = [&](int gi, float v, float c) -> bool {
+        if (!(v >= kAlphaMin)) return false;
         const float alpha = fminf(kAlphaMax, v);
         const float Tn = T[m] * (1.f - alpha);
         if (Tn < kTMin) {
           act[m] = false;
           stop = gi;
-          break;
+          return true;
         }
-        const float c = ch[m] == 0 ? cl.x : (ch[m] == 1 ? cl.y : cl.z);
         acc[m] += c * alpha * T[m];
         T[m] = Tn;
+        return false;
+      };
+      int q = 0;
+      for (; q + 2 <= cnt; q += 2) {
+        const int g0 = idx[q], g1 = idx[q + 1];
+        const float4 c0 = s_co[g0];
+        const float4 c1 = s_co[g1];
+        const float2 u0 = mrow[g0];
+        const float2 u1 = mrow[g1];
+        const float dx0 = px[m] - u0.x, dy0 = py[m] - u0.y;
+        const float dx1 = px[m] - u1.x, dy1 = py[m] - u1.y;
+        const float p0 = quad_power(c0.x, c0.y, c0.z, dx0, dy0);
+        const float p1 = quad_power(c1.x, c1.y, c1.z, dx1, dy1);
+        const bool h0 = p0 <= 0.f && p0 >= c0.w;
+        const bool h1 = p1 <= 0.f && p1 >= c1.w;
+        if (!(h0 || h1)) continue;
+        const float2 o0 = orow[g0];
+        const float2 o1 = orow[g1];
+        const float v0 = h0 ? o0.x * ex2_approx(p0) : 0.f;
+        const float v1 = h1 ? o1.x * ex2_approx(p1) : 0.f;
+        if (apply(g0, v0, o0.y)) {
+          stop_q = q;
+          break;
+        }
+        if (apply(g1, v1, o1.y)) {
+          stop_q = q + 1;
+          break;
+        }
       }
+      if (stop < 0 && q < cnt) {
+        const int gi = idx[q];
+        const float4 co = s_co[gi];
+        const float2 mu = mrow[gi];
+        const float dx = px[m] - mu.x;
+        const float dy = py[m] - mu.y;
+        const float power = quad_power(co.x, co.y, co.z, dx, dy);
+        if (power <= 0.f && power >= co.w) {
+          const float2 oc = orow[gi];
+          if (apply(gi, oc.x * ex2_approx(power), oc.y)) stop_q = q;
+        }
+      }
+      if (COUNT) n_eval += stop_q >= 0 ? (unsigned long long)(stop_q + 1) : (unsigned long long)cnt;
       // list entries walked in this batch, skipped ones included
       if (COUNT) n_visit += stop >= 0 ? (unsigned long long)(stop + 1) : (unsigned long long)nbatch;
     }
@@ -204,12 +238,48 @@ __global__ void __launch_bounds__(256) k_blend(PanelGeom g, BlendArgs a) {
   }
 }
 
+template <int R, bool COUNT>
+__global__ void __launch_bounds__(256) k_blend(PanelGeom g, BlendArgs a) {
+  extern __shared__ float4 smem[];
+  if (a.P_dev && *a.P_dev > a.P_cap) return;  // capacity overflow: leave the image
+  const int k = blockIdx.x / g.T;
+  const int t = blockIdx.x - k * g.T;
+  blend_run<R, COUNT>(g, a, k, t, a.ranges[(size_t)t * g.K + k], smem);
+}
+
+// Batched, persistent form: a grid sized to the GPU pulls (scene, cluster,
+// tile) runs from a work counter until all scenes' runs are done.
+template <int R>
+__global__ void __launch_bounds__(256) k_blend_batch(BatchBlendArgs b) {
+  extern __shared__ float4 smem[];
+  __shared__ uint32_t s_run;
+  if (b.P_dev && *b.P_dev > b.P_cap) return;  // capacity overflow: leave the images
+  for (;;) {
+    if (threadIdx.x == 0) s_run = atomicAdd(b.work, 1u);
+    __syncthreads();
+    const uint32_t r = s_run;
+    __syncthreads();
+    if (r >= b.total_runs) break;
+    int si = 0;
+    while (si + 1 < b.n_scenes && r >= b.sc[si + 1].run_base) ++si;
+    const SceneBlend& sc = b.sc[si];
+    const uint32_t local = r - sc.run_base;
+    const int k = (int)(local / (uint32_t)sc.g.T);
+    const int t = (int)(local - (uint32_t)k * (uint32_t)sc.g.T);
+    const uint2 rg = b.ranges[(size_t)(sc.g.tile_base + t) * b.K_glob + k];
+    blend_run<R, false>(sc.g, sc.a, k, t, rg, smem);
+  }
+}
+
+size_t blend_smem_bytes(int C, int block) {
+  const int nw = block / 32;
+  return (size_t)block * (sizeof(float4) + 3 * sizeof(float2) + C * sizeof(float2)) +
+         (((size_t)C * block + 1) & ~(size_t)1) * sizeof(uint16_t) + (size_t)C * (nw + 1) * sizeof(int);
+}
+
 template <int R>
 cudaError_t launch_r(const PanelGeom& g, const BlendArgs& a, int block, cudaStream_t s) {
-  const int nw = block / 32;
-  const size_t smem = (size_t)block * (2 * sizeof(float4) + g.C * sizeof(float2)) +
-                      (((size_t)g.C * block + 1) & ~(size_t)1) * sizeof(uint16_t) +
-                      (size_t)g.C * (nw + 1) * sizeof(int);
+  const size_t smem = blend_smem_bytes(g.C, block);
   const unsigned grid = (unsigned)((int64_t)g.K * g.T);
   if (a.eval_counter) {
     if (smem > 48 * 1024)
@@ -225,13 +295,64 @@ cudaError_t launch_r(const PanelGeom& g, const BlendArgs& a, int block, cudaStre
   return cudaGetLastError();
 }
 
+
+template <int R>
+cudaError_t launch_batch_r(const BatchBlendArgs& b, int block, int C_max, cudaStream_t s) {
+  const size_t smem = blend_smem_bytes(C_max, block);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_blend_batch<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_blend_batch<R>, block, smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t want = (int64_t)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+  const unsigned grid = (unsigned)(want < (int64_t)b.total_runs ? want : (int64_t)b.total_runs);
+  if (grid == 0) return cudaSuccess;
+  k_blend_batch<R><<<grid, block, smem, s>>>(b);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+// Subpixels per thread: the requested count when its block fits 256 threads,
+// else the smallest power of two from 2 up that does.
+static int choose_r(int need, int requested) {
+  if (requested > 0 && (need + requested - 1) / requested <= 256) return requested;
+  int R = 2;
+  while (R < 8 && (need + R - 1) / R > 256) R *= 2;
+  return R;
+}
+
+cudaError_t launch_blend_batch(const BatchBlendArgs& b, int max_segment, int C_max,
+                               int subpixels_per_thread, cudaStream_t s) {
+  if (b.total_runs == 0) return cudaSuccess;
+  const int need = max_segment > 0 ? max_segment : 1;
+  const int R = choose_r(need, subpixels_per_thread);
+  int block = (need + R - 1) / R;
+  block = ((block + 31) / 32) * 32;
+  if (block > 256) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(b.work, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  switch (R) {
+    case 1:
+      return launch_batch_r<1>(b, block, C_max, s);
+    case 2:
+      return launch_batch_r<2>(b, block, C_max, s);
+    case 4:
+      return launch_batch_r<4>(b, block, C_max, s);
+    default:
+      return launch_batch_r<8>(b, block, C_max, s);
+  }
+}
 
 cudaError_t launch_blend(const PanelGeom& g, const BlendArgs& a, cudaStream_t s) {
   if ((int64_t)g.K * g.T == 0) return cudaSuccess;
   const int need = a.max_segment > 0 ? a.max_segment : 1;
-  int R = 2;
-  while (R < 8 && (need + R - 1) / R > 256) R *= 2;
+  const int R = choose_r(need, a.subpixels_per_thread);
   int block = (need + R - 1) / R;
   block = ((block + 31) / 32) * 32;
   if (block > 256) return cudaErrorInvalidValue;

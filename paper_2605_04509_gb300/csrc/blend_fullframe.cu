@@ -16,15 +16,10 @@ constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTMin = 1e-4f;
 
-__device__ __forceinline__ float ex2_approx(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
 // Grid: (view j, tile t), view-major; clusters are single views (C = 1).
 template <bool COUNT>
 __global__ void __launch_bounds__(512) k_blend_fullframe(PanelGeom g, BlendArgs a) {
+  if (a.P_dev && *a.P_dev > a.P_cap) return;  // capacity overflow: leave the image
   extern __shared__ float4 smem[];
   const int NB = blockDim.x;
   float4* s_co = smem;
@@ -60,7 +55,7 @@ __global__ void __launch_bounds__(512) k_blend_fullframe(PanelGeom g, BlendArgs 
       const float2 mu = s_mean[gi];
       const float dx = px - mu.x;
       const float dy = py - mu.y;
-      const float power = co.x * dx * dx + co.z * dy * dy + co.y * dx * dy;
+      const float power = quad_power(co.x, co.y, co.z, dx, dy);
       if (power > 0.f) continue;
       const float v = co.w * ex2_approx(power);
       if (!(v >= kAlphaMin)) continue;

@@ -16,14 +16,9 @@ constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTMin = 1e-4f;
 
-__device__ __forceinline__ float ex2_approx(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
 template <bool COUNT>
 __global__ void __launch_bounds__(256) k_blend_raster(PanelGeom g, BlendArgs a) {
+  if (a.P_dev && *a.P_dev > a.P_cap) return;  // capacity overflow: leave the image
   const int t = blockIdx.x;
   const int tx = t % g.TX, ty = t / g.TX;
   const int w = min(g.TW, g.W - tx * g.TW);
@@ -50,7 +45,7 @@ __global__ void __launch_bounds__(256) k_blend_raster(PanelGeom g, BlendArgs a) 
       const float2 mu = reinterpret_cast<const float2*>(a.means2d)[rec * g.C + slot];
       const float dx = px - mu.x;
       const float dy = py - mu.y;
-      const float power = co.x * dx * dx + co.z * dy * dy + co.y * dx * dy;
+      const float power = quad_power(co.x, co.y, co.z, dx, dy);
       if (power > 0.f) continue;
       const float v = co.w * ex2_approx(power);
       if (!(v >= kAlphaMin)) continue;

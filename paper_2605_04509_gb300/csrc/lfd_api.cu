@@ -100,7 +100,7 @@ struct lfd_plan {
   DevBuf pair_key[2], pair_val[2];
   DevBuf radix_tmp;
   DevBuf ranges;
-  DevBuf small;  // [0] total pairs, [1] eval counter
+  DevBuf small;  // [0] total pairs, [1], [2] evaluation counters, [3] wait-error bits
   DevBuf host_in[5];  // device copies of host Gaussians (lfd_render_host)
   DevBuf image;       // device image for lfd_render_host
   DevBuf g_means2d, g_conic, g_color, g_opac;  // backward scratch
@@ -123,6 +123,11 @@ struct lfd_plan {
   bool ev_has_project[2] = {false, false};
   double acc_ms[4] = {0, 0, 0, 0};
   int64_t acc_frames = 0;
+  // capacity mode (lfd_plan_reserve): buffers preallocated for cap_M
+  // Gaussians and cap_P pairs; frames then never allocate, synchronise or
+  // read back, so they can be captured into a CUDA graph
+  int64_t cap_M = 0;
+  int64_t cap_P = 0;
   // full-frame baseline: a child plan with one view per cluster whose blend
   // renders whole per-view images (created on first use)
   bool fullframe = false;
@@ -145,6 +150,18 @@ int fold_stage_times(lfd_plan* p, int set) {
   return LFD_OK;
 }
 
+// A bounded device wait (the sort's bulk-copy waits) that gave up leaves bit 0 in
+// the plan's error word; it is reported once, at the next read-back.
+// (An overflow bit left by an earlier capacity-mode frame is cleared too.)
+int take_wait_error(lfd_plan* p, cudaStream_t s) {
+  const uint32_t bits = (uint32_t)(p->h_small[3] & 0xffffffffull);
+  if (!bits) return LFD_OK;
+  p->h_small[3] = 0;
+  LFD_CUDA(cudaMemsetAsync(p->small.as<unsigned long long>() + 3, 0, sizeof(unsigned long long), s));
+  if (!(bits & 1u)) return LFD_OK;
+  return fail(LFD_ERR_TIMEOUT, "a bounded device wait of the sort gave up; the previous frame is wrong");
+}
+
 }  // namespace
 
 namespace lfd {
@@ -162,6 +179,8 @@ int plan_view(const lfd_plan* p, PlanView* out) {
   out->bg[1] = p->opts.bg[1];
   out->bg[2] = p->opts.bg[2];
   out->h_small = p->h_small;
+  out->subpixels_per_thread = p->opts.subpixels_per_thread;
+  out->fullframe = p->fullframe;
   return LFD_OK;
 }
 
@@ -189,6 +208,8 @@ const char* lfd_status_string(int status) {
       return "CUDA error";
     case LFD_ERR_STATE:
       return "requested data does not exist";
+    case LFD_ERR_TIMEOUT:
+      return "a bounded device wait gave up";
     default:
       return "unknown status";
   }
@@ -238,6 +259,9 @@ int lfd_plan_create(const lfd_panel* panel, const lfd_opts* opts, lfd_plan** out
   if (O.remap != 0 && O.remap != 1) return fail(LFD_ERR_INVALID, "remap must be 0 or 1");
   if (O.sort_mode != LFD_SORT_DEPTH_FIRST && O.sort_mode != LFD_SORT_KEY64)
     return fail(LFD_ERR_INVALID, "unknown sort_mode");
+  if (O.subpixels_per_thread != 0 && O.subpixels_per_thread != 1 && O.subpixels_per_thread != 2 &&
+      O.subpixels_per_thread != 4 && O.subpixels_per_thread != 8)
+    return fail(LFD_ERR_INVALID, "subpixels_per_thread must be 0, 1, 2, 4 or 8");
 
   lfd_plan* p = new (std::nothrow) lfd_plan();
   if (!p) return fail(LFD_ERR_OOM, "host allocation failed");
@@ -279,6 +303,9 @@ int lfd_plan_create(const lfd_panel* panel, const lfd_opts* opts, lfd_plan** out
   if ((e = cudaMallocHost(&p->h_small, 4 * sizeof(unsigned long long))) != cudaSuccess)
     return cleanup(fail_cuda(e, "cudaMallocHost"));
   if ((rc = p->small.ensure(4 * sizeof(unsigned long long))) != LFD_OK) return cleanup(rc);
+  memset(p->h_small, 0, 4 * sizeof(unsigned long long));
+  if ((e = cudaMemset(p->small.p, 0, 4 * sizeof(unsigned long long))) != cudaSuccess)
+    return cleanup(fail_cuda(e, "cudaMemset"));
   for (auto& set : p->ev)
     for (cudaEvent_t& ev : set)
       if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cleanup(fail_cuda(e, "cudaEventCreate"));
@@ -432,12 +459,15 @@ static int render_projected_impl(lfd_plan* p, int64_t M, const float* means2d,
     return fail(LFD_ERR_INVALID, "NULL attribute buffer");
   if (M > 0 && (!aligned(conic_opacity, 16) || !aligned(color_tau, 16) || !aligned(means2d, 8)))
     return fail(LFD_ERR_INVALID, "attribute buffers misaligned");
-  const bool timing = (p->flags & LFD_FLAG_STAGE_TIMING) != 0;
-  const bool counting = (p->flags & LFD_FLAG_COUNT_EVALS) != 0;
+  const bool capmode = p->cap_P > 0;
+  if (capmode && M > p->cap_M) return fail(LFD_ERR_CAPACITY, "more Gaussians than reserved");
+  const bool timing = (p->flags & LFD_FLAG_STAGE_TIMING) != 0 && !capmode;
+  const bool counting = (p->flags & LFD_FLAG_COUNT_EVALS) != 0 && !capmode;
   const bool key64 = p->opts.sort_mode == LFD_SORT_KEY64;
   const int64_t n_items = (int64_t)g.K * M;
   int rc;
   unsigned long long* d_small = p->small.as<unsigned long long>();
+  uint32_t* d_err = reinterpret_cast<uint32_t*>(d_small + 3);
   const int es = p->ev_set;
   cudaEvent_t* ev = p->ev[es];
   if (timing) {
@@ -464,7 +494,7 @@ static int render_projected_impl(lfd_plan* p, int64_t M, const float* means2d,
     bool alt = false;
     LFD_CUDA(radix_sort_u64(p->item_key[0].as<uint64_t>(), p->item_key[1].as<uint64_t>(),
                             p->item_val[0].as<uint32_t>(), p->item_val[1].as<uint32_t>(), n_items,
-                            0, 32 + g.bit_k, p->radix_tmp.p, &alt, s));
+                            nullptr, 0, 32 + g.bit_k, p->radix_tmp.p, &alt, d_err, s));
     order = p->item_val[alt ? 1 : 0].as<uint32_t>();
   }
   // tile counts and union descriptors in natural (cluster, Gaussian) order:
@@ -477,11 +507,18 @@ static int render_projected_impl(lfd_plan* p, int64_t M, const float* means2d,
     LFD_CUDA(launch_gather_u32(p->counts_nat.as<uint32_t>(), order, n_items, p->counts.as<uint32_t>(), s));
   LFD_CUDA(scan_exclusive(p->counts.as<uint32_t>(), p->offsets.as<uint32_t>(), n_items, p->scan_tmp.p,
                           d_small, s));
-  LFD_CUDA(cudaMemcpyAsync(p->h_small, d_small, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-  LFD_CUDA(cudaStreamSynchronize(s));
-  if ((rc = fold_stage_times(p, es ^ 1)) != LFD_OK) return rc;
-  const unsigned long long P = p->h_small[0];
-  if (P >= 0xffffffffull) return fail(LFD_ERR_CAPACITY, "more than 2^32 - 1 Gaussian-tile pairs");
+  unsigned long long P = (unsigned long long)p->cap_P;
+  if (!capmode) {
+    LFD_CUDA(cudaMemcpyAsync(p->h_small, d_small, 4 * sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost, s));
+    LFD_CUDA(cudaStreamSynchronize(s));
+    if ((rc = fold_stage_times(p, es ^ 1)) != LFD_OK) return rc;
+    if ((rc = take_wait_error(p, s)) != LFD_OK) return rc;
+    P = p->h_small[0];
+    if (P >= 0xffffffffull) return fail(LFD_ERR_CAPACITY, "more than 2^32 - 1 Gaussian-tile pairs");
+  }
+  // from here on P bounds the pair count; the kernels read the exact count
+  // (and, in capacity mode, whether it fits) from d_small[0]
   const size_t kbytes = key64 ? 8 : 4;
   for (int b = 0; b < 2; ++b) {
     if ((rc = p->pair_key[b].ensure((size_t)(P + 1) * kbytes)) != LFD_OK) return rc;
@@ -493,7 +530,8 @@ static int render_projected_impl(lfd_plan* p, int64_t M, const float* means2d,
                                 p->counts.as<uint32_t>(), p->offsets.as<uint32_t>(),
                                 key64 ? nullptr : p->pair_key[0].as<uint32_t>(),
                                 key64 ? p->pair_key[0].as<uint64_t>() : nullptr,
-                                p->pair_val[0].as<uint32_t>(), p->bin_desc.p, s));
+                                p->pair_val[0].as<uint32_t>(), p->bin_desc.p, d_small, P, d_err,
+                                s));
   if (timing) LFD_CUDA(cudaEventRecord(ev[2], s));
 
   // ---- stage 3: sort by (tile, cluster, depth) ----
@@ -503,14 +541,13 @@ static int render_projected_impl(lfd_plan* p, int64_t M, const float* means2d,
   if (key64)
     LFD_CUDA(radix_sort_u64(p->pair_key[0].as<uint64_t>(), p->pair_key[1].as<uint64_t>(),
                             p->pair_val[0].as<uint32_t>(), p->pair_val[1].as<uint32_t>(), (int64_t)P,
-                            0, 32 + g.bit_k + g.bit_t, p->radix_tmp.p, &alt, s));
+                            d_small, 0, 32 + g.bit_k + g.bit_t, p->radix_tmp.p, &alt, d_err, s));
   else
     LFD_CUDA(radix_sort_u32(p->pair_key[0].as<uint32_t>(), p->pair_key[1].as<uint32_t>(),
                             p->pair_val[0].as<uint32_t>(), p->pair_val[1].as<uint32_t>(), (int64_t)P,
-                            g.bit_k, g.bit_k + g.bit_t, p->radix_tmp.p, &alt, s));
+                            d_small, g.bit_k, g.bit_k + g.bit_t, p->radix_tmp.p, &alt, d_err, s));
   const int kb = alt ? 1 : 0;
-  LFD_CUDA(cudaMemsetAsync(p->ranges.p, 0, (size_t)g.T * g.K * sizeof(uint2), s));
-  LFD_CUDA(launch_ranges(g, (int64_t)P, key64 ? nullptr : p->pair_key[kb].as<uint32_t>(),
+  LFD_CUDA(launch_ranges(g, (int64_t)P, d_small, key64 ? nullptr : p->pair_key[kb].as<uint32_t>(),
                          key64 ? p->pair_key[kb].as<uint64_t>() : nullptr, p->ranges.as<uint2>(), s));
   if (timing) LFD_CUDA(cudaEventRecord(ev[3], s));
 
@@ -532,6 +569,9 @@ static int render_projected_impl(lfd_plan* p, int64_t M, const float* means2d,
   ba.eval_counter = counting ? d_small + 1 : nullptr;
   ba.max_segment = p->max_segment;
   ba.V = p->V;
+  ba.P_dev = d_small;
+  ba.P_cap = P;
+  ba.subpixels_per_thread = p->opts.subpixels_per_thread;
   if (p->fullframe)
     LFD_CUDA(launch_blend_fullframe(g, ba, s));
   else if (p->opts.remap)
@@ -545,7 +585,7 @@ static int render_projected_impl(lfd_plan* p, int64_t M, const float* means2d,
     p->ev_set = es ^ 1;
   }
 
-  p->last_P = (int64_t)P;
+  p->last_P = capmode ? -2 : (int64_t)P;  // -2: the count is on the device
   p->last_M = M;
   p->last_from_render = projected_here;
   p->last_key_buf = kb;
@@ -553,7 +593,7 @@ static int render_projected_impl(lfd_plan* p, int64_t M, const float* means2d,
   p->last_sort_mode = p->opts.sort_mode;
   p->last_stream = s;
   if (stats) {
-    stats->num_pairs = (int64_t)P;
+    stats->num_pairs = capmode ? -1 : (int64_t)P;
     stats->num_visits = -1;
     stats->num_evals = -1;
     stats->ms_project = stats->ms_keygen = stats->ms_sort = stats->ms_blend = -1.f;
@@ -738,14 +778,76 @@ int lfd_render_host(lfd_plan* p, const lfd_gaussians* gh, const lfd_camera* cams
   return LFD_OK;
 }
 
+int lfd_plan_reserve(lfd_plan* p, int64_t max_gaussians, int64_t max_pairs) {
+  if (!p) return fail(LFD_ERR_INVALID, "NULL plan");
+  if (max_gaussians < 0 || max_pairs < 0) return fail(LFD_ERR_INVALID, "negative capacity");
+  if (p->fullframe) return fail(LFD_ERR_INVALID, "capacity mode is for the subpixel path");
+  if (max_pairs == 0) {
+    p->cap_M = p->cap_P = 0;
+    return LFD_OK;
+  }
+  const PanelGeom& g = p->g;
+  if (max_pairs >= 0xffffffffll) return fail(LFD_ERR_CAPACITY, "more than 2^32 - 1 pairs");
+  if ((uint64_t)max_gaussians * (uint64_t)g.K >= (1ull << 32))
+    return fail(LFD_ERR_CAPACITY, "M * K must stay below 2^32");
+  const int64_t n = (int64_t)g.K * max_gaussians;
+  int rc;
+  const size_t items4 = (size_t)(n + 1) * 4;
+  const size_t sort_tmp = radix_temp_bytes(n) > radix_temp_bytes(max_pairs) ? radix_temp_bytes(n)
+                                                                            : radix_temp_bytes(max_pairs);
+  if ((rc = p->proj_means.ensure((size_t)(n * g.C + 1) * 8)) != LFD_OK ||
+      (rc = p->proj_co.ensure((size_t)(n + 1) * 16)) != LFD_OK ||
+      (rc = p->proj_ct.ensure((size_t)(n + 1) * 16)) != LFD_OK ||
+      (rc = p->proj_depth.ensure(items4)) != LFD_OK || (rc = p->counts.ensure(items4)) != LFD_OK ||
+      (rc = p->offsets.ensure(items4)) != LFD_OK || (rc = p->counts_nat.ensure(items4)) != LFD_OK ||
+      (rc = p->scan_tmp.ensure(scan_temp_bytes(n + 1))) != LFD_OK ||
+      (rc = p->bin_desc.ensure((size_t)(n + 1) * kBinDescBytes)) != LFD_OK ||
+      (rc = p->radix_tmp.ensure(sort_tmp)) != LFD_OK ||
+      (rc = p->ranges.ensure((size_t)g.T * g.K * sizeof(uint2))) != LFD_OK)
+    return rc;
+  for (int b = 0; b < 2; ++b) {
+    if ((rc = p->item_key[b].ensure((size_t)(n + 1) * 8)) != LFD_OK ||
+        (rc = p->item_val[b].ensure(items4)) != LFD_OK ||
+        (rc = p->pair_key[b].ensure((size_t)(max_pairs + 1) * 8)) != LFD_OK ||
+        (rc = p->pair_val[b].ensure((size_t)(max_pairs + 1) * 4)) != LFD_OK)
+      return rc;
+  }
+  p->cap_M = max_gaussians;
+  p->cap_P = max_pairs;
+  return LFD_OK;
+}
+
+int lfd_plan_status(lfd_plan* p, int64_t* pairs) {
+  if (!p) return fail(LFD_ERR_INVALID, "NULL plan");
+  LFD_CUDA(cudaDeviceSynchronize());
+  unsigned long long h[4];
+  LFD_CUDA(cudaMemcpy(h, p->small.p, sizeof(h), cudaMemcpyDeviceToHost));
+  if (pairs) *pairs = (int64_t)h[0];
+  const uint32_t bits = (uint32_t)(h[3] & 0xffffffffull);
+  if (!bits) return LFD_OK;
+  LFD_CUDA(cudaMemset(p->small.as<unsigned long long>() + 3, 0, sizeof(unsigned long long)));
+  if (bits & 1u) return fail(LFD_ERR_TIMEOUT, "a bounded device wait of the sort gave up");
+  char msg[160];
+  snprintf(msg, sizeof(msg), "a frame had more pairs than reserved (last frame: %llu, reserved: %lld)",
+           h[0], (long long)p->cap_P);
+  return fail(LFD_ERR_CAPACITY, msg);
+}
+
 int lfd_plan_copy_lists(const lfd_plan* p, uint32_t* list, uint32_t* ranges, uint64_t* keys,
                         int64_t capacity) {
   if (!p) return fail(LFD_ERR_INVALID, "NULL plan");
-  if (p->last_P < 0) return fail(LFD_ERR_STATE, "no frame rendered yet");
+  if (p->last_P == -1) return fail(LFD_ERR_STATE, "no frame rendered yet");
   if (keys && p->last_sort_mode != LFD_SORT_KEY64)
     return fail(LFD_ERR_STATE, "keys exist only with LFD_SORT_KEY64");
   LFD_CUDA(cudaStreamSynchronize(p->last_stream));
-  const int64_t P = p->last_P;
+  int64_t P = p->last_P;
+  if (P == -2) {  // capacity mode: the count is on the device
+    LFD_CUDA(cudaDeviceSynchronize());
+    unsigned long long h = 0;
+    LFD_CUDA(cudaMemcpy(&h, p->small.p, sizeof(h), cudaMemcpyDeviceToHost));
+    if ((int64_t)h > p->cap_P) return fail(LFD_ERR_CAPACITY, "the last frame overflowed its capacity");
+    P = (int64_t)h;
+  }
   if ((list || keys) && capacity < P) return fail(LFD_ERR_INVALID, "capacity below the pair count");
   if (list && P > 0)
     LFD_CUDA(cudaMemcpy(list, p->pair_val[p->last_val_buf].p, (size_t)P * 4, cudaMemcpyDeviceToHost));

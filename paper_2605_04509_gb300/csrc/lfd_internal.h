@@ -26,6 +26,11 @@ struct PanelGeom {
   int TW, TH, TX, TY, T;
   int cap;  // 3 * TW * TH
   int bit_k, bit_t;
+  // Offsets of this panel's tiles and clusters in a batch's global tile and
+  // cluster numbering (0 for a single scene): pair keys carry the global
+  // tile, item keys the global cluster.
+  int tile_base = 0;
+  int cluster_base = 0;
 };
 
 // ---- plan tables (plan_kernels.cu) ----
@@ -71,34 +76,61 @@ cudaError_t launch_bin_emit(const PanelGeom& g, int64_t M, const float* means2d,
                             uint32_t* vals, const void* desc, cudaStream_t s);
 // emission from descriptors indexed by item r (written by a natural-order
 // count pass); items visited in `order`, counts/offsets indexed by position
+// Writes nothing when *P_dev > P_cap (P_dev non-null); then sets bit 1 of
+// *err (capacity overflow).
 cudaError_t launch_bin_emit_coop(const PanelGeom& g, int64_t M, const float* means2d,
                                  const float* conic_opacity, const float* color_tau,
                                  const float* depth, const uint32_t* order, int64_t n_items,
                                  const uint32_t* counts, const uint32_t* offsets, uint32_t* keys32,
-                                 uint64_t* keys64, uint32_t* vals, const void* desc, cudaStream_t s);
+                                 uint64_t* keys64, uint32_t* vals, const void* desc,
+                                 const unsigned long long* P_dev, unsigned long long P_cap,
+                                 uint32_t* err, cudaStream_t s);
 // dst[s] = src[idx[s]]
 cudaError_t launch_gather_u32(const uint32_t* src, const uint32_t* idx, int64_t n, uint32_t* dst,
                               cudaStream_t s);
-cudaError_t launch_ranges(const PanelGeom& g, int64_t P, const uint32_t* keys32,
-                          const uint64_t* keys64, uint2* ranges, cudaStream_t s);
+// [S_tk, E_tk) of every (tile, cluster) run by binary search in the sorted
+// keys (empty runs get (0, 0)); P a capacity, the live count from *P_dev
+// when non-null. Writes the whole table.
+cudaError_t launch_ranges(const PanelGeom& g, int64_t P, const unsigned long long* P_dev,
+                          const uint32_t* keys32, const uint64_t* keys64, uint2* ranges,
+                          cudaStream_t s);
 
 // ---- scan and radix sort (sort.cu) ----
 size_t scan_temp_bytes(int64_t n);
 // exclusive scan of n uint32 into out; the 64-bit total goes to *total_dev
 cudaError_t scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, void* temp,
                            unsigned long long* total_dev, cudaStream_t s);
+// bytes of sort scratch for up to n items (n the capacity)
 size_t radix_temp_bytes(int64_t n);
-// stable LSD radix sort of (key, value) by key bits [begin_bit, end_bit);
+// Stable LSD radix sort of (key, value) by key bits [begin_bit, end_bit);
 // ping-pongs between the two buffers; *result_in_alt tells where the result
-// ends up
+// ends up (it depends on the bit range only). n is a host-side capacity;
+// when n_dev is non-null the sort covers min(*n_dev, n) items, so the count
+// may be produced on the device by the preceding kernels. A bulk-copy wait
+// that reaches its bound sets bit 0 of *err (the result is then wrong).
 cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals,
-                           uint32_t* vals_alt, int64_t n, int begin_bit, int end_bit, void* temp,
-                           bool* result_in_alt, cudaStream_t s);
+                           uint32_t* vals_alt, int64_t n, const unsigned long long* n_dev,
+                           int begin_bit, int end_bit, void* temp, bool* result_in_alt,
+                           uint32_t* err, cudaStream_t s);
 cudaError_t radix_sort_u64(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals,
-                           uint32_t* vals_alt, int64_t n, int begin_bit, int end_bit, void* temp,
-                           bool* result_in_alt, cudaStream_t s);
+                           uint32_t* vals_alt, int64_t n, const unsigned long long* n_dev,
+                           int begin_bit, int end_bit, void* temp, bool* result_in_alt,
+                           uint32_t* err, cudaStream_t s);
 
 // ---- blend (blend.cu) ----
+// 2^x on the special-function unit (hand-written PTX instruction).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+// -q/2 * log2(e) for the pre-scaled conic (A, B, C) = -log2(e) (a/2, b, c/2):
+// A dx^2 + B dx dy + C dy^2 in one fixed order of rounded operations, shared
+// by every blend kernel and the backward replay so that they agree bit for
+// bit.
+__device__ __forceinline__ float quad_power(float A, float B, float C, float dx, float dy) {
+  return fmaf(dx, fmaf(B, dy, __fmul_rn(A, dx)), __fmul_rn(__fmul_rn(C, dy), dy));
+}
 struct BlendArgs {
   const uint32_t* psi;  // [T][cap] packed (view << 16) | local index
   const int32_t* seg;   // [T][K+1]
@@ -113,8 +145,33 @@ struct BlendArgs {
   unsigned long long* eval_counter;  // non-null: [0] visited entries, [1] evaluated ones
   int max_segment;
   const uint8_t* V;  // view index [H][W][3] (raster-order blend)
+  // capacity mode: the blend writes nothing when *P_dev > P_cap
+  const unsigned long long* P_dev = nullptr;
+  unsigned long long P_cap = 0;
+  int subpixels_per_thread = 0;  // 0: automatic
 };
 cudaError_t launch_blend(const PanelGeom& g, const BlendArgs& a, cudaStream_t s);
+
+// Batched blend: several scenes (each with its own panel tables, attributes
+// and image) in one persistent launch over all their (cluster, tile) runs.
+constexpr int kMaxBatchScenes = 16;
+struct SceneBlend {
+  PanelGeom g;        // tile_base: first global tile of the scene
+  BlendArgs a;        // the scene's tables, attributes and image
+  uint32_t run_base;  // first global run (runs of a scene are k * T + t)
+};
+struct BatchBlendArgs {
+  SceneBlend sc[kMaxBatchScenes];
+  int n_scenes;
+  uint32_t total_runs;
+  int K_glob;            // clusters per tile in the global range table
+  const uint2* ranges;   // [global tiles][K_glob]
+  unsigned int* work;    // work counter (zeroed by the launcher)
+  const unsigned long long* P_dev;
+  unsigned long long P_cap;
+};
+cudaError_t launch_blend_batch(const BatchBlendArgs& b, int max_segment, int C_max,
+                               int subpixels_per_thread, cudaStream_t s);
 // the same blend without the view-coherent remap (threads in raster order)
 cudaError_t launch_blend_raster(const PanelGeom& g, const BlendArgs& a, cudaStream_t s);
 // full-frame baseline: per-view pixel blend fused with the interlacing
@@ -148,6 +205,8 @@ struct PlanView {
   const uint8_t* V;
   float bg[3];
   unsigned long long* h_small;  // pinned host words owned by the plan
+  int subpixels_per_thread;
+  bool fullframe;
 };
 int plan_view(const lfd_plan* p, PlanView* out);
 int set_error(int code, const char* msg);

@@ -112,6 +112,7 @@ extern "C" int lfd_render_projected_noalloc(lfd_plan* plan, int64_t M, const flo
                            reinterpret_cast<uint32_t*>(sb + kOffPairVal) + kNaPairs};
   uint2* ranges = reinterpret_cast<uint2*>(sb + kOffRanges);
   unsigned long long* d_small = reinterpret_cast<unsigned long long*>(sb + kOffSmall);
+  uint32_t* d_err = reinterpret_cast<uint32_t*>(d_small + 3);  // zero at load
   void* temp = sb + kOffRadix;
   if (radix_temp_bytes(kNaPairs) > kRadixBytes || radix_temp_bytes(kNaItems) > kRadixBytes ||
       scan_temp_bytes(kNaItems + 1) > kRadixBytes)
@@ -122,16 +123,24 @@ extern "C" int lfd_render_projected_noalloc(lfd_plan* plan, int64_t M, const flo
   if (!key64) {
     NA_CUDA(launch_item_keys(g, M, depth, color_tau, item_key[0], item_val[0], s));
     bool alt = false;
-    NA_CUDA(radix_sort_u64(item_key[0], item_key[1], item_val[0], item_val[1], n_items, 0,
-                           32 + g.bit_k, temp, &alt, s));
+    NA_CUDA(radix_sort_u64(item_key[0], item_key[1], item_val[0], item_val[1], n_items, nullptr,
+                           0, 32 + g.bit_k, temp, &alt, d_err, s));
     order = item_val[alt ? 1 : 0];
   }
   NA_CUDA(launch_bin_count(g, M, means2d, conic_opacity, color_tau, order, n_items, counts,
                            nullptr, s));
   NA_CUDA(scan_exclusive(counts, offsets, n_items, temp, d_small, s));
-  NA_CUDA(cudaMemcpyAsync(pv.h_small, d_small, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  NA_CUDA(cudaMemcpyAsync(pv.h_small, d_small, 4 * sizeof(unsigned long long),
+                          cudaMemcpyDeviceToHost, s));
   NA_CUDA(cudaStreamSynchronize(s));
   const unsigned long long P = pv.h_small[0];
+  if (pv.h_small[3] & 0xffffffffull) {
+    // a bounded wait of this call's item sort (or of an earlier call's pair
+    // sort) gave up: reported here, once
+    pv.h_small[3] = 0;
+    NA_CUDA(cudaMemsetAsync(d_err, 0, sizeof(unsigned long long), s));
+    return na_fail(LFD_ERR_TIMEOUT, "a bounded device wait of the sort gave up");
+  }
   if (P > (unsigned long long)kNaPairs)
     return na_fail(LFD_ERR_CAPACITY,
                    "lfd_render_projected_noalloc: more than 131072 Gaussian-tile pairs");
@@ -143,16 +152,15 @@ extern "C" int lfd_render_projected_noalloc(lfd_plan* plan, int64_t M, const flo
   // sort by (tile, cluster, depth)
   bool alt = false;
   if (key64)
-    NA_CUDA(radix_sort_u64(pk64[0], pk64[1], pair_val[0], pair_val[1], (int64_t)P, 0,
-                           32 + g.bit_k + g.bit_t, temp, &alt, s));
+    NA_CUDA(radix_sort_u64(pk64[0], pk64[1], pair_val[0], pair_val[1], (int64_t)P, nullptr, 0,
+                           32 + g.bit_k + g.bit_t, temp, &alt, d_err, s));
   else
-    NA_CUDA(radix_sort_u32(pk32[0], pk32[1], pair_val[0], pair_val[1], (int64_t)P, g.bit_k,
-                           g.bit_k + g.bit_t, temp, &alt, s));
+    NA_CUDA(radix_sort_u32(pk32[0], pk32[1], pair_val[0], pair_val[1], (int64_t)P, nullptr,
+                           g.bit_k, g.bit_k + g.bit_t, temp, &alt, d_err, s));
   const int kb = alt ? 1 : 0;
-  // the range table must start at zero: the array keeps the last call's data
-  NA_CUDA(cudaMemsetAsync(ranges, 0, (size_t)g.T * g.K * sizeof(uint2), s));
-  NA_CUDA(launch_ranges(g, (int64_t)P, key64 ? nullptr : pk32[kb], key64 ? pk64[kb] : nullptr,
-                        ranges, s));
+  // the range kernel writes every entry of the table
+  NA_CUDA(launch_ranges(g, (int64_t)P, nullptr, key64 ? nullptr : pk32[kb],
+                        key64 ? pk64[kb] : nullptr, ranges, s));
   // blend
   BlendArgs ba;
   ba.psi = pv.psi;

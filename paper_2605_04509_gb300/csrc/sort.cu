@@ -3,12 +3,18 @@
 // contiguous and depth-ordered; Alg. 1 stage 3).
 //
 // Radix sort: reduce-then-scan per 8-bit digit. Pass = (1) per-tile digit
-// histogram, (2) exclusive scan of the digit-major histogram table, which
-// yields every tile's global base per digit, (3) stable scatter. Inside a
-// tile each warp ranks its items with match-any peer masks in (round, lane)
-// order and per-warp digit counters, then the warps' counters are prefixed,
-// so the scatter preserves input order among equal digits (stability).
-// No kernel waits on another block, so nothing can spin.
+// histogram into a digit-major table, (2) exclusive scan of that table, which
+// yields every tile's global output base per digit, (3) stable scatter. The
+// scatter kernel is persistent: each block walks its share of the tiles and,
+// while it ranks one tile, the bulk-copy engine (cp.async.bulk, completion on
+// an mbarrier) fetches the block's next tile into the other half of a double
+// buffer in shared memory. Inside a tile each warp ranks its items with
+// ballot peer masks in (round, lane) order and per-warp digit counters, the
+// warps' counters are prefixed, and the items are scattered through shared
+// memory so that each digit's run is written with consecutive addresses.
+// No block waits on another block. The item count may be given on the device
+// (n_dev) with a host-side capacity bounding it, so that no host read-back is
+// needed between key generation and the sort.
 #include "lfd_internal.h"
 
 namespace lfd {
@@ -17,13 +23,6 @@ namespace {
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;
-
-constexpr int kRadixBits = 8;
-constexpr int kRadix = 1 << kRadixBits;
-constexpr int kSortThreads = 256;
-constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortRounds = 16;
-constexpr int kSortTile = kSortThreads * kSortRounds;  // 4096 items
 
 __global__ void __launch_bounds__(kScanThreads)
     k_scan_reduce(const uint32_t* __restrict__ in, int64_t n, unsigned long long* __restrict__ bsum) {
@@ -120,83 +119,239 @@ __global__ void __launch_bounds__(kScanThreads)
   }
 }
 
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortRounds = 16;
+constexpr int kSortTile = kSortThreads * kSortRounds;  // 4096 items
+constexpr int kSpinLimit = 1 << 22;                   // polls of an mbarrier before giving up
+constexpr unsigned long long kWaitNs = 250000000ull;  // or 0.25 s, whichever comes first
+
 template <typename K>
 __device__ __forceinline__ int digit_of(K key, int shift, int mask) {
   return (int)((key >> shift) & (K)mask);
 }
 
-template <typename K>
-__global__ void __launch_bounds__(kSortThreads)
-    k_radix_hist(const K* __restrict__ keys, int64_t n, int shift, int mask,
-                 uint32_t* __restrict__ hist, int64_t nb) {
-  __shared__ uint32_t s_cnt[kRadix];
-  for (int a = threadIdx.x; a < kRadix; a += kSortThreads) s_cnt[a] = 0;
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int64_t base = (int64_t)blockIdx.x * kSortTile;
-#pragma unroll 4
-  for (int r = 0; r < kSortRounds; ++r) {
-    const int64_t idx = base + r * kSortThreads + threadIdx.x;
-    const int d = idx < n ? digit_of(keys[idx], shift, mask) : kRadix;
-    const unsigned peers = __match_any_sync(0xffffffffu, d);
-    if (d < kRadix && lane == __ffs(peers) - 1) atomicAdd(&s_cnt[d], (uint32_t)__popc(peers));
-  }
-  __syncthreads();
-  for (int a = threadIdx.x; a < kRadix; a += kSortThreads)
-    hist[(int64_t)a * nb + blockIdx.x] = s_cnt[a];
+__device__ __forceinline__ int64_t live_count(int64_t n_cap, const unsigned long long* n_dev) {
+  if (!n_dev) return n_cap;
+  const unsigned long long v = *n_dev;
+  return v < (unsigned long long)n_cap ? (int64_t)v : n_cap;
 }
 
-// Stable scatter of one tile. Items are ranked in the tile (warp chunks in
-// order, match-any ranks inside a warp round, warp counters prefixed across
-// warps), placed in shared memory in digit order, and written out so that
-// consecutive threads store consecutive addresses of each digit's run.
+// Per-tile digit histogram, written digit-major: hist[d * nb + tile]. A
+// thread counts 16 consecutive keys, so the lanes of a warp look at keys far
+// apart and their shared-memory increments rarely collide; each warp counts
+// into its own histogram. Tiles past the live count write zeros.
 template <typename K>
 __global__ void __launch_bounds__(kSortThreads)
-    k_radix_scatter(const K* __restrict__ kin, K* __restrict__ kout, const uint32_t* __restrict__ vin,
-                    uint32_t* __restrict__ vout, int64_t n, int shift, int mask,
-                    const uint32_t* __restrict__ hist_scanned, int64_t nb) {
+    k_rts_hist(const K* __restrict__ keys, int64_t n_cap, const unsigned long long* __restrict__ n_dev,
+               int shift, int mask, uint32_t* __restrict__ hist, int64_t nb) {
+  __shared__ uint32_t s_h[kSortWarps][kRadix];
+  const int warp = threadIdx.x >> 5;
+  for (int a = threadIdx.x; a < kSortWarps * kRadix; a += kSortThreads) (&s_h[0][0])[a] = 0;
+  __syncthreads();
+  const int64_t n = live_count(n_cap, n_dev);
+  const int64_t tile0 = (int64_t)blockIdx.x * kSortTile;
+  const int64_t c0 = tile0 + (int64_t)threadIdx.x * kSortRounds;
+  if (c0 < n) {
+    const bool vec = (reinterpret_cast<uintptr_t>(keys) & 15) == 0;
+    if (vec && c0 + kSortRounds <= n) {
+      const uint4* src = reinterpret_cast<const uint4*>(keys + c0);
+      constexpr int NV = kSortRounds * (int)sizeof(K) / 16;
+      uint4 q[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) q[v] = src[v];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        if constexpr (sizeof(K) == 4) {
+          atomicAdd(&s_h[warp][digit_of((K)q[v].x, shift, mask)], 1u);
+          atomicAdd(&s_h[warp][digit_of((K)q[v].y, shift, mask)], 1u);
+          atomicAdd(&s_h[warp][digit_of((K)q[v].z, shift, mask)], 1u);
+          atomicAdd(&s_h[warp][digit_of((K)q[v].w, shift, mask)], 1u);
+        } else {
+          atomicAdd(&s_h[warp][digit_of((K)(((uint64_t)q[v].y << 32) | q[v].x), shift, mask)], 1u);
+          atomicAdd(&s_h[warp][digit_of((K)(((uint64_t)q[v].w << 32) | q[v].z), shift, mask)], 1u);
+        }
+      }
+    } else {
+      const int cnt = (int)min((int64_t)kSortRounds, n - c0);
+      for (int r = 0; r < cnt; ++r) atomicAdd(&s_h[warp][digit_of(keys[c0 + r], shift, mask)], 1u);
+    }
+  }
+  __syncthreads();
+  const int d = threadIdx.x;
+  uint32_t sum = 0;
+#pragma unroll
+  for (int w = 0; w < kSortWarps; ++w) sum += s_h[w][d];
+  hist[(int64_t)d * nb + blockIdx.x] = sum;
+}
+
+// Peer mask of the lanes holding the same digit, from one ballot per digit
+// bit (and one for validity).
+__device__ __forceinline__ unsigned digit_peers(int d, bool valid) {
+  unsigned m = __ballot_sync(0xffffffffu, valid);
+  m = valid ? m : ~m;
+#pragma unroll
+  for (int b = 0; b < kRadixBits; ++b) {
+    const bool bit = (d >> b) & 1;
+    const unsigned bb = __ballot_sync(0xffffffffu, bit);
+    m &= bit ? bb : ~bb;
+  }
+  return m;
+}
+
+// ---- bulk-copy and mbarrier helpers (inline PTX) ----
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// global -> shared bulk copy (both 16-byte aligned, bytes a multiple of 16),
+// completion counted on the mbarrier
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait for one phase of an mbarrier: false once kWaitNs nanoseconds
+// have passed (or kSpinLimit polls, whichever comes first).
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, uint32_t parity) {
+  const unsigned long long t0 = global_ns();
+  for (int i = 0; i < kSpinLimit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 15) == 15 && global_ns() - t0 > kWaitNs) return false;
+    if (i > 16) __nanosleep(32);
+  }
+  return false;
+}
+
+// Stable scatter of one pass. Block b handles tiles b, b + G, b + 2G, ...
+// (G = gridDim.x); tile t's output base per digit is hscan[d * nb + t].
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads)
+    k_rts_scatter(const K* __restrict__ kin, K* __restrict__ kout, const uint32_t* __restrict__ vin,
+                  uint32_t* __restrict__ vout, int64_t n_cap, const unsigned long long* __restrict__ n_dev,
+                  int shift, int mask, const uint32_t* __restrict__ hscan, int64_t nb,
+                  uint32_t* __restrict__ err) {
   static_assert(kRadix == kSortThreads, "one digit per thread");
-  extern __shared__ __align__(16) unsigned char s_raw[];
-  K* s_key = reinterpret_cast<K*>(s_raw);
+  extern __shared__ __align__(128) unsigned char s_raw[];
+  // [in0 keys][in0 vals][in1 keys][in1 vals][out keys][out vals]
+  constexpr size_t kBuf = (size_t)kSortTile * (sizeof(K) + sizeof(uint32_t));
+  auto in_key = [&](int b) { return reinterpret_cast<K*>(s_raw + b * kBuf); };
+  auto in_val = [&](int b) {
+    return reinterpret_cast<uint32_t*>(s_raw + b * kBuf + kSortTile * sizeof(K));
+  };
+  K* s_key = reinterpret_cast<K*>(s_raw + 2 * kBuf);
   uint32_t* s_val = reinterpret_cast<uint32_t*>(s_key + kSortTile);
   __shared__ uint32_t s_wcnt[kSortWarps][kRadix];
   __shared__ uint32_t s_base[kRadix];
   __shared__ uint32_t s_dstart[kRadix];
   __shared__ uint32_t s_wsum[kSortWarps];
+  __shared__ __align__(8) unsigned long long s_bar[2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
-  for (int a = threadIdx.x; a < kSortWarps * kRadix; a += kSortThreads) (&s_wcnt[0][0])[a] = 0;
-  s_base[threadIdx.x] = hist_scanned[(int64_t)threadIdx.x * nb + blockIdx.x];
-  __syncthreads();
-  // warp w owns the contiguous chunk [base, base + 32 * kSortRounds)
-  const int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * 32 * kSortRounds;
-  K key[kSortRounds];
-  uint32_t val[kSortRounds];
-  uint32_t rk[kSortRounds];
-  int dg[kSortRounds];
-#pragma unroll
-  for (int r = 0; r < kSortRounds; ++r) {
-    const int64_t idx = base + r * 32 + lane;
-    int d = kRadix;
-    if (idx < n) {
-      key[r] = kin[idx];
-      val[r] = vin[idx];
-      d = digit_of(key[r], shift, mask);
+  const int64_t n = live_count(n_cap, n_dev);
+  const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
+  const int d = threadIdx.x;
+  // bulk copies need 16-byte aligned sources; otherwise every tile is loaded
+  // with plain loads
+  const bool bulk_ok =
+      ((reinterpret_cast<uintptr_t>(kin) | reinterpret_cast<uintptr_t>(vin)) & 15) == 0;
+  auto is_full = [&](int64_t t) { return bulk_ok && (t + 1) * kSortTile <= n; };
+  // start the bulk copy of tile t into buffer b (thread 0)
+  auto fetch = [&](int b, int64_t t) {
+    if (t < ntiles && is_full(t)) {
+      // the buffer's last readers finished before the preceding barrier
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(&s_bar[b], (uint32_t)kBuf);
+      bulk_g2s(in_key(b), kin + t * kSortTile, (uint32_t)(kSortTile * sizeof(K)), &s_bar[b]);
+      bulk_g2s(in_val(b), vin + t * kSortTile, (uint32_t)(kSortTile * sizeof(uint32_t)), &s_bar[b]);
     }
-    const unsigned peers = __match_any_sync(0xffffffffu, d);
-    const int rank = __popc(peers & lt);
-    const int cnt = __popc(peers);
-    const uint32_t b = d < kRadix ? s_wcnt[warp][d] : 0u;
-    __syncwarp();
-    if (d < kRadix && rank == cnt - 1) s_wcnt[warp][d] = b + (uint32_t)cnt;
-    __syncwarp();
-    rk[r] = b + (uint32_t)rank;
-    dg[r] = d;
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fetch(0, blockIdx.x);
   }
   __syncthreads();
-  // per digit: exclusive prefix over warps, then the block-wide digit starts
-  {
-    const int d = threadIdx.x;
+  uint32_t parity = 0u;  // bit b: phase parity awaited on buffer b
+  int b = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t tile0 = tile * kSortTile;
+    const int cnt = (int)min((int64_t)kSortTile, n - tile0);
+    for (int a = threadIdx.x; a < kSortWarps * kRadix; a += kSortThreads) (&s_wcnt[0][0])[a] = 0;
+    s_base[d] = hscan[(int64_t)d * nb + tile];
+    if (threadIdx.x == 0) fetch(b ^ 1, tile + gridDim.x);
+    if (is_full(tile)) {
+      const uint32_t ph = (parity >> b) & 1u;
+      if (!mbar_wait_bounded(&s_bar[b], ph)) {
+        atomicOr(err, 1u);
+        mbar_wait_bounded(&s_bar[b], ph);
+      }
+      parity ^= 1u << b;
+    } else {
+      K* kk = in_key(b);
+      uint32_t* vv = in_val(b);
+      for (int j = threadIdx.x; j < cnt; j += kSortThreads) {
+        kk[j] = kin[tile0 + j];
+        vv[j] = vin[tile0 + j];
+      }
+    }
+    __syncthreads();
+    // rank: warp w owns the contiguous chunk [w * 32 * kSortRounds, ...)
+    const K* ik = in_key(b);
+    const uint32_t* iv = in_val(b);
+    uint32_t rk[kSortRounds];
+    int dg[kSortRounds];
+#pragma unroll
+    for (int r = 0; r < kSortRounds; ++r) {
+      const int idx = warp * 32 * kSortRounds + r * 32 + lane;
+      const bool valid = idx < cnt;
+      const int dd = valid ? digit_of(ik[idx], shift, mask) : kRadix;
+      const unsigned peers = digit_peers(dd, valid);
+      const int rank = __popc(peers & lt);
+      const int pc = __popc(peers);
+      const uint32_t bw = valid ? s_wcnt[warp][dd] : 0u;
+      __syncwarp();
+      if (valid && rank == pc - 1) s_wcnt[warp][dd] = bw + (uint32_t)pc;
+      __syncwarp();
+      rk[r] = bw + (uint32_t)rank;
+      dg[r] = dd;
+    }
+    __syncthreads();
     uint32_t run = 0;
 #pragma unroll
     for (int w = 0; w < kSortWarps; ++w) {
@@ -204,58 +359,79 @@ __global__ void __launch_bounds__(kSortThreads)
       s_wcnt[w][d] = run;
       run += c;
     }
-    uint32_t x = run;
+    {
+      uint32_t x = run;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (lane == 31) s_wsum[warp] = x;
+      __syncthreads();
+      uint32_t pre = 0;
+      for (int w = 0; w < warp; ++w) pre += s_wsum[w];
+      s_dstart[d] = pre + x - run;
     }
-    if (lane == 31) s_wsum[warp] = x;
     __syncthreads();
-    uint32_t pre = 0;
-    for (int w = 0; w < warp; ++w) pre += s_wsum[w];
-    s_dstart[d] = pre + x - run;
-  }
-  __syncthreads();
 #pragma unroll
-  for (int r = 0; r < kSortRounds; ++r) {
-    const int d = dg[r];
-    if (d < kRadix) {
-      const uint32_t pos = s_dstart[d] + s_wcnt[warp][d] + rk[r];
-      s_key[pos] = key[r];
-      s_val[pos] = val[r];
+    for (int r = 0; r < kSortRounds; ++r) {
+      const int dd = dg[r];
+      if (dd < kRadix) {
+        const int idx = warp * 32 * kSortRounds + r * 32 + lane;
+        const uint32_t pos = s_dstart[dd] + s_wcnt[warp][dd] + rk[r];
+        s_key[pos] = ik[idx];
+        s_val[pos] = iv[idx];
+      }
     }
-  }
-  __syncthreads();
-  const int64_t tile0 = (int64_t)blockIdx.x * kSortTile;
-  const int cnt = (int)min((int64_t)kSortTile, n - tile0);
-  for (int j = threadIdx.x; j < cnt; j += kSortThreads) {
-    const K k = s_key[j];
-    const int d = digit_of(k, shift, mask);
-    const uint32_t out = s_base[d] + ((uint32_t)j - s_dstart[d]);
-    kout[out] = k;
-    vout[out] = s_val[j];
+    __syncthreads();
+    for (int j = threadIdx.x; j < cnt; j += kSortThreads) {
+      const K k = s_key[j];
+      const int dd = digit_of(k, shift, mask);
+      const uint32_t out = s_base[dd] + ((uint32_t)j - s_dstart[dd]);
+      if ((int64_t)out < n) {
+        kout[out] = k;
+        vout[out] = s_val[j];
+      }
+    }
+    __syncthreads();  // buffers and counters are reused by the next tile
+    b ^= 1;
   }
 }
 
 template <typename K>
-cudaError_t radix_sort_impl(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt, int64_t n,
-                            int begin_bit, int end_bit, void* temp, bool* result_in_alt,
-                            cudaStream_t s) {
+constexpr size_t scatter_smem() {
+  return (size_t)kSortTile * (sizeof(K) + sizeof(uint32_t)) * 3;
+}
+
+// resident blocks of the scatter kernel (its persistent grid)
+template <typename K>
+int scatter_grid(int64_t tiles) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rts_scatter<K>, kSortThreads,
+                                                scatter_smem<K>());
+  const int64_t g = (int64_t)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+  return (int)(g < tiles ? g : (tiles > 0 ? tiles : 1));
+}
+
+template <typename K>
+cudaError_t radix_sort_impl(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt, int64_t n_cap,
+                            const unsigned long long* n_dev, int begin_bit, int end_bit, void* temp,
+                            bool* result_in_alt, uint32_t* err, cudaStream_t s) {
   *result_in_alt = false;
-  if (n <= 1 || end_bit <= begin_bit) return cudaSuccess;
-  const int64_t nb = (n + kSortTile - 1) / kSortTile;
+  if (n_cap <= 1 || end_bit <= begin_bit) return cudaSuccess;
+  const int64_t nb = (n_cap + kSortTile - 1) / kSortTile;
   uint32_t* hist = reinterpret_cast<uint32_t*>(temp);
   uint32_t* hscan = hist + nb * kRadix;
   void* stemp = hscan + nb * kRadix;
   unsigned long long* total = reinterpret_cast<unsigned long long*>(
       reinterpret_cast<char*>(stemp) + scan_temp_bytes(nb * kRadix));
-  const size_t smem = (size_t)kSortTile * (sizeof(K) + sizeof(uint32_t));
-  {
-    cudaError_t e = cudaFuncSetAttribute(k_radix_scatter<K>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  const size_t smem = scatter_smem<K>();
+  cudaError_t e =
+      cudaFuncSetAttribute(k_rts_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = scatter_grid<K>(nb);
   K* src_k = keys;
   K* dst_k = keys_alt;
   uint32_t* src_v = vals;
@@ -264,17 +440,14 @@ cudaError_t radix_sort_impl(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals
   for (int shift = begin_bit; shift < end_bit; shift += kRadixBits) {
     const int nbits = end_bit - shift < kRadixBits ? end_bit - shift : kRadixBits;
     const int mask = (1 << nbits) - 1;
-    k_radix_hist<K><<<(unsigned)nb, kSortThreads, 0, s>>>(src_k, n, shift, mask, hist, nb);
+    k_rts_hist<K><<<(unsigned)nb, kSortThreads, 0, s>>>(src_k, n_cap, n_dev, shift, mask, hist, nb);
     note_launches(1);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    e = scan_exclusive(hist, hscan, nb * kRadix, stemp, total, s);
-    if (e != cudaSuccess) return e;
-    k_radix_scatter<K><<<(unsigned)nb, kSortThreads, smem, s>>>(src_k, dst_k, src_v, dst_v, n,
-                                                                shift, mask, hscan, nb);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = scan_exclusive(hist, hscan, nb * kRadix, stemp, total, s)) != cudaSuccess) return e;
+    k_rts_scatter<K><<<(unsigned)grid, kSortThreads, smem, s>>>(src_k, dst_k, src_v, dst_v, n_cap,
+                                                                n_dev, shift, mask, hscan, nb, err);
     note_launches(1);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     K* tk = src_k;
     src_k = dst_k;
     dst_k = tk;
@@ -285,6 +458,16 @@ cudaError_t radix_sort_impl(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals
   }
   *result_in_alt = alt;
   return cudaSuccess;
+}
+
+// Self-test kernel: one thread waits, with the bound, on an mbarrier phase
+// that nothing completes.
+__global__ void k_selftest_wait(uint32_t* err) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (!mbar_wait_bounded(&bar, 0u)) atomicOr(err, 1u);
 }
 
 }  // namespace
@@ -315,17 +498,41 @@ size_t radix_temp_bytes(int64_t n) {
 }
 
 cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals,
-                           uint32_t* vals_alt, int64_t n, int begin_bit, int end_bit, void* temp,
-                           bool* result_in_alt, cudaStream_t s) {
-  return radix_sort_impl<uint32_t>(keys, keys_alt, vals, vals_alt, n, begin_bit, end_bit, temp,
-                                   result_in_alt, s);
+                           uint32_t* vals_alt, int64_t n, const unsigned long long* n_dev,
+                           int begin_bit, int end_bit, void* temp, bool* result_in_alt,
+                           uint32_t* err, cudaStream_t s) {
+  return radix_sort_impl<uint32_t>(keys, keys_alt, vals, vals_alt, n, n_dev, begin_bit, end_bit,
+                                   temp, result_in_alt, err, s);
 }
 
 cudaError_t radix_sort_u64(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals,
-                           uint32_t* vals_alt, int64_t n, int begin_bit, int end_bit, void* temp,
-                           bool* result_in_alt, cudaStream_t s) {
-  return radix_sort_impl<uint64_t>(keys, keys_alt, vals, vals_alt, n, begin_bit, end_bit, temp,
-                                   result_in_alt, s);
+                           uint32_t* vals_alt, int64_t n, const unsigned long long* n_dev,
+                           int begin_bit, int end_bit, void* temp, bool* result_in_alt,
+                           uint32_t* err, cudaStream_t s) {
+  return radix_sort_impl<uint64_t>(keys, keys_alt, vals, vals_alt, n, n_dev, begin_bit, end_bit,
+                                   temp, result_in_alt, err, s);
 }
 
 }  // namespace lfd
+
+// Self-test of the bounded device waits: a kernel waits on an mbarrier phase
+// that nothing completes (no copy is started, no thread arrives). The wait
+// must give up after its bound, set the error bit and let the kernel end.
+extern "C" LFD_API int lfd_selftest_wait_timeout(void* stream) {
+  using namespace lfd;
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t* err = nullptr;
+  cudaError_t e = cudaMalloc(&err, 4);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, 4, s);
+  if (e == cudaSuccess) {
+    k_selftest_wait<<<1, 32, 0, s>>>(err);
+    note_launches(1);
+    e = cudaGetLastError();
+  }
+  uint32_t bits = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, err, 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(err);
+  if (e != cudaSuccess) return set_cuda_error(e, "wait self-test");
+  return (bits & 1u) ? LFD_ERR_TIMEOUT : LFD_OK;
+}

@@ -21,6 +21,7 @@ LFD_ERR_OOM = -2
 LFD_ERR_CAPACITY = -3
 LFD_ERR_CUDA = -4
 LFD_ERR_STATE = -5
+LFD_ERR_TIMEOUT = -6
 SORT_DEPTH_FIRST = 0
 SORT_KEY64 = 1
 FLAG_STAGE_TIMING = 1
@@ -41,7 +42,8 @@ class CPanel(ct.Structure):
 class COpts(ct.Structure):
     _fields_ = [("tile_w", ct.c_int32), ("tile_h", ct.c_int32),
                 ("views_per_cluster", ct.c_int32), ("remap", ct.c_int32),
-                ("sort_mode", ct.c_int32), ("bg", ct.c_float * 3)]
+                ("sort_mode", ct.c_int32), ("bg", ct.c_float * 3),
+                ("subpixels_per_thread", ct.c_int32)]
 
 
 DTYPE_F32 = 0
@@ -113,6 +115,14 @@ def load() -> ct.CDLL:
                                       _P, _P, ct.POINTER(CStats)], ct.c_int),
             "lfd_plan_copy_lists": ([_P, _P, _P, _P, ct.c_int64], ct.c_int),
             "lfd_get_stage_totals": ([_P, ct.POINTER(CStageTotals), ct.c_int32], ct.c_int),
+            "lfd_plan_reserve": ([_P, ct.c_int64, ct.c_int64], ct.c_int),
+            "lfd_plan_status": ([_P, ct.POINTER(ct.c_int64)], ct.c_int),
+            "lfd_batch_create": ([ct.POINTER(_P), ct.c_int32, ct.POINTER(_P)], ct.c_int),
+            "lfd_batch_destroy": ([_P], None),
+            "lfd_batch_reserve": ([_P, ct.POINTER(ct.c_int64), ct.c_int64], ct.c_int),
+            "lfd_batch_render": ([_P, _P, _P, _P, _P], ct.c_int),
+            "lfd_batch_status": ([_P, ct.POINTER(ct.c_int64)], ct.c_int),
+            "lfd_selftest_wait_timeout": ([_P], ct.c_int),
             "lfd_kernel_launches": ([], ct.c_uint64),
             "lfd_status_string": ([ct.c_int], ct.c_char_p),
             "lfd_last_error": ([], ct.c_char_p),
@@ -189,13 +199,15 @@ class Plan:
     """A panel + options plan (lfd_plan_create); owns V, Psi and scratch."""
 
     def __init__(self, panel, tile: Tuple[int, int] = (16, 16), views_per_cluster: int = 8,
-                 sort_mode: int = SORT_DEPTH_FIRST, bg=(0.0, 0.0, 0.0), remap: bool = True):
+                 sort_mode: int = SORT_DEPTH_FIRST, bg=(0.0, 0.0, 0.0), remap: bool = True,
+                 subpixels_per_thread: int = 0):
         L = load()
         self.panel = panel
         cp = CPanel(panel.width, panel.height, panel.num_views, float(panel.tan_slant),
                     float(panel.pitch), float(panel.k_offset))
         co = COpts(tile[0], tile[1], views_per_cluster, 1 if remap else 0, sort_mode,
-                   (ct.c_float * 3)(*bg))
+                   (ct.c_float * 3)(*bg), subpixels_per_thread)
+        self.subpixels_per_thread = subpixels_per_thread
         h = _P()
         _check(L.lfd_plan_create(ct.byref(cp), ct.byref(co), ct.byref(h)))
         self._h = h
@@ -323,6 +335,24 @@ class Plan:
                                       _stream_ptr(stream), ct.byref(st)))
         return out_host, st.as_dict()
 
+    def reserve(self, max_gaussians: int, max_pairs: int):
+        """lfd_plan_reserve: capacity mode (no read-back; graph-capturable
+        frames). max_pairs = 0 leaves capacity mode."""
+        _check(load().lfd_plan_reserve(self._h, int(max_gaussians), int(max_pairs)))
+
+    def status(self) -> int:
+        """lfd_plan_status: raises LFDError on overflow / wait timeout;
+        returns the last frame's pair count."""
+        P = ct.c_int64(0)
+        _check(load().lfd_plan_status(self._h, ct.byref(P)))
+        return int(P.value)
+
+    def status_code(self) -> Tuple[int, int]:
+        """(status code, last pair count) of lfd_plan_status, without raising."""
+        P = ct.c_int64(0)
+        rc = load().lfd_plan_status(self._h, ct.byref(P))
+        return rc, int(P.value)
+
     def stage_totals(self, reset: bool = False) -> Dict[str, float]:
         t = CStageTotals()
         _check(load().lfd_get_stage_totals(self._h, ct.byref(t), 1 if reset else 0))
@@ -376,3 +406,60 @@ def render_autograd(plan: "Plan", cams: np.ndarray, means, scales, quats, opacit
             return g["means"], g["scales"], g["quats"], g["opacities"], g["sh"]
 
     return _Render.apply(means, scales, quats, opacities, sh)
+
+
+class Batch:
+    """Several scenes rendered per frame (lfd_batch_*): plans[s] gives scene
+    s's panel; plans may repeat. Always in capacity mode (reserve first)."""
+
+    def __init__(self, plans):
+        L = load()
+        self.plans = list(plans)  # keeps the plans alive for the batch
+        arr = (_P * len(self.plans))(*[p._h for p in self.plans])
+        h = _P()
+        _check(L.lfd_batch_create(arr, len(self.plans), ct.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().lfd_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reserve(self, max_gaussians, max_pairs: int):
+        arr = (ct.c_int64 * len(self.plans))(*[int(m) for m in max_gaussians])
+        _check(load().lfd_batch_reserve(self._h, arr, int(max_pairs)))
+
+    def images(self):
+        import torch
+        return [torch.empty((p.panel.height, p.panel.width, 3), dtype=torch.float32, device="cuda")
+                for p in self.plans]
+
+    def render(self, scenes, cams_list, outs=None, stream=None):
+        """scenes: list of device scene dicts; cams_list: list of [N_s, 16]
+        float32 camera arrays. Returns the list of images (no sync)."""
+        n = len(self.plans)
+        outs = outs if outs is not None else self.images()
+        gs = (CGaussians * n)(*[gaussians_struct(sc) for sc in scenes])
+        carrs = [cameras_array(c)[0] for c in cams_list]
+        self._keep = carrs  # the host arrays must live through the call
+        cptrs = (_P * n)(*[ct.cast(a, _P) for a in carrs])
+        optrs = (_P * n)(*[_dptr(o) for o in outs])
+        _check(load().lfd_batch_render(self._h, ct.cast(gs, _P), ct.cast(cptrs, _P),
+                                       ct.cast(optrs, _P), _stream_ptr(stream)))
+        return outs
+
+    def status(self) -> int:
+        P = ct.c_int64(0)
+        _check(load().lfd_batch_status(self._h, ct.byref(P)))
+        return int(P.value)
+
+    def status_code(self) -> Tuple[int, int]:
+        P = ct.c_int64(0)
+        rc = load().lfd_batch_status(self._h, ct.byref(P))
+        return rc, int(P.value)
