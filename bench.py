@@ -39,7 +39,7 @@ WORKLOAD_TEXT = ("paper4k: 1M Gaussians (64-blob mixture, radius 10), 45 views o
                  "cone at radius 30, 3840x2160 panel, slant 0.2 rad, pitch 5.3 subpixels, "
                  "|V_k|=8 (K=6), SH degree 3, FP32")
 # tile shapes the default run's autotuner tries (paper_2605_04509_gb300.autotune)
-AUTOTUNE_TILES = ((16, 16), (32, 16), (32, 8), (16, 8))
+AUTOTUNE_TILES = ((16, 16), (24, 16), (32, 16), (32, 8))
 # FP32 peak of the blend's pipe: 152 SMs x 128 FP32 lanes x 2070 MHz max SM clock
 SMS, FP32_LANES, SM_MAX_MHZ, MUFU_LANES = 152, 128, 2070.0, 16
 # algorithmic FP32 operations per visited (subpixel, Gaussian) evaluation:
@@ -298,7 +298,7 @@ def run_ours(args):
         tile = (int(choice[0]), int(choice[1]))
         autotune = {"chosen": f"{tile[0]}x{tile[1]}",
                     "ms_per_frame": {f"{r['tile'][0]}x{r['tile'][1]}": round(r["ms"], 3)
-                                     for r in res["results"]}}
+                                     for r in res["results"] if "ms" in r}}
     else:
         tile = tuple(int(v) for v in args.tile.split("x"))
     tile_text = f"{tile[0]}x{tile[1]}"

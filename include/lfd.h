@@ -314,13 +314,15 @@ LFD_API int lfd_plan_status(lfd_plan *plan, int64_t *pairs);
  * Alg. 1 for up to 16 scenes, each with its own plan (panel, tiles,
  * clusters; several scenes may share one plan), Gaussians, cameras and
  * image. Projection and per-item binning run per scene; the item sort, the
- * offsets scan, the pair sort (Eq. 11 keys over a global tile numbering:
- * scene s owns the tiles after those of scenes 0..s-1) and the range search
- * run once for all scenes, and one persistent blend kernel takes the
- * (scene, cluster, tile) runs from a work counter. Each scene's image equals
- * the single-scene lfd_render of that scene bit for bit.
+ * offsets scan, the pair sort and the range search run once for all scenes
+ * (pair key = tile << (bits(S) + bits(K_max)) | scene << bits(K_max) |
+ * cluster, sorted on the tile bits only: the pairs are emitted scene-major,
+ * so every (scene, tile, cluster) run comes out contiguous), and one
+ * persistent blend kernel takes the (scene, cluster, tile) runs from a work
+ * counter. Each scene's image equals the single-scene lfd_render of that
+ * scene bit for bit.
  * Plans must use LFD_SORT_DEPTH_FIRST, remap = 1 and the same
- * subpixels_per_thread; the global tile and cluster bits must fit 32.
+ * subpixels_per_thread; the tile, scene and cluster bits must fit 32.
  * The batch keeps pointers to the plans (their V, Psi and run tables): the
  * plans must outlive it. A batch always runs in capacity mode:
  * lfd_batch_reserve (per-scene Gaussian capacities [num_scenes], total pair

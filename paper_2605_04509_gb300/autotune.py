@@ -66,6 +66,10 @@ def tune(panel, scene, cams, views_per_cluster: int = 8,
             try:
                 _, st = plan.render(scene, cams, out)
                 ms = time_plan(plan, scene, cams, out, frames, warmup)
+            except lfd.LFDError as e:  # e.g. more pairs than 2^32 with small tiles
+                results.append({"tile": list(tile), "subpixels_per_thread": spt,
+                                "skipped": str(e)})
+                continue
             finally:
                 plan.close()
             img = out.clamp(0, 1)
@@ -78,7 +82,10 @@ def tune(panel, scene, cams, views_per_cluster: int = 8,
                             "pairs": int(st["num_pairs"]), "max_diff": diff})
             if diff > tol:
                 raise RuntimeError(f"tile {tile} / {spt}: image differs by {diff}")
-    best = min(results, key=lambda r: r["ms"])
+    timed_ok = [r for r in results if "ms" in r]
+    if not timed_ok:
+        raise RuntimeError("no candidate configuration could render this scene")
+    best = min(timed_ok, key=lambda r: r["ms"])
     return {"best": best, "results": results}
 
 

@@ -2,10 +2,13 @@
 // plan (panel tables V, Psi and the per-(tile, cluster) runs), Gaussians,
 // cameras and image. Projection and the per-item binning run per scene; the
 // item sort, the offsets scan, the pair sort, the range search and the blend
-// each run once over all scenes, in a global tile space where scene s owns
-// tiles [tile_base_s, tile_base_s + T_s) and clusters [cluster_base_s,
-// cluster_base_s + K_s) (pair key = (global tile << bit_k) | k, bit_k from the
-// largest K of the batch; item key = (global cluster << 32) | depth bits).
+// each run once over all scenes. Item keys carry a global cluster number
+// (scene s owns clusters [cluster_base_s, cluster_base_s + K_s)), so the items
+// and hence the emitted pairs come out scene-major. A pair's key is
+// (t << (bit_s + bit_kc)) | (s << bit_kc) | k with t the scene's own tile: the
+// stable sort on the tile bits alone then yields (tile, scene, cluster,
+// depth) order, and every (scene, tile, cluster) run is contiguous - with as
+// many sort passes as the largest panel's tile count needs.
 // The blend is one persistent launch that pulls (scene, cluster, tile) runs
 // from a work counter. A batch always runs in capacity mode: every buffer is
 // sized by lfd_batch_reserve, and a frame neither allocates nor synchronises
@@ -64,10 +67,10 @@ struct lfd_batch {
   int n = 0;
   lfd_plan* plans[kMaxBatchScenes] = {};
   PlanView pv[kMaxBatchScenes];
-  PanelGeom g[kMaxBatchScenes];  // with global tile/cluster bases and key bits
+  PanelGeom g[kMaxBatchScenes];  // with the scene key code, cluster base and key bits
   uint32_t run_base[kMaxBatchScenes + 1] = {};
-  int T_total = 0, K_glob = 0, clusters_total = 0, C_max = 0, max_segment = 0, spt = 0;
-  int bit_k = 0, bit_t = 0, bit_cluster = 0;
+  int T_max = 0, K_glob = 0, clusters_total = 0, C_max = 0, max_segment = 0, spt = 0;
+  int bit_kc = 0, bit_s = 0, bit_t = 0, bit_cluster = 0;
   // capacities
   int64_t cap_M[kMaxBatchScenes] = {};
   int64_t cap_items = 0, cap_P = 0;
@@ -118,7 +121,7 @@ int lfd_batch_create(lfd_plan* const* plans, int32_t num_scenes, lfd_batch** out
   lfd_batch* b = new (std::nothrow) lfd_batch();
   if (!b) return bfail(LFD_ERR_OOM, "host allocation failed");
   b->n = num_scenes;
-  int64_t tiles = 0, runs = 0;
+  int64_t runs = 0;
   int spt = -1;
   for (int s = 0; s < num_scenes; ++s) {
     if (plan_view(plans[s], &b->pv[s]) != LFD_OK) {
@@ -137,29 +140,30 @@ int lfd_batch_create(lfd_plan* const* plans, int32_t num_scenes, lfd_batch** out
     spt = v.subpixels_per_thread;
     b->plans[s] = plans[s];
     b->g[s] = v.g;
-    b->g[s].tile_base = (int)tiles;
     b->g[s].cluster_base = b->clusters_total;
     b->run_base[s] = (uint32_t)runs;
-    tiles += v.g.T;
     runs += (int64_t)v.g.T * v.g.K;
     b->clusters_total += v.g.K;
+    b->T_max = v.g.T > b->T_max ? v.g.T : b->T_max;
     b->K_glob = v.g.K > b->K_glob ? v.g.K : b->K_glob;
     b->C_max = v.g.C > b->C_max ? v.g.C : b->C_max;
     b->max_segment = v.max_segment > b->max_segment ? v.max_segment : b->max_segment;
   }
   b->spt = spt;
   b->run_base[num_scenes] = (uint32_t)runs;
-  b->T_total = (int)tiles;
-  b->bit_k = ceil_log2_u((uint64_t)b->K_glob);
-  b->bit_t = ceil_log2_u((uint64_t)tiles);
+  b->bit_kc = ceil_log2_u((uint64_t)b->K_glob);
+  b->bit_s = ceil_log2_u((uint64_t)num_scenes);
+  b->bit_t = ceil_log2_u((uint64_t)b->T_max);
   b->bit_cluster = ceil_log2_u((uint64_t)b->clusters_total);
-  if (b->bit_k + b->bit_t > 32 || runs >= (1ll << 32) || tiles * b->K_glob >= (1ll << 31)) {
+  if (b->bit_t + b->bit_s + b->bit_kc > 32 || runs >= (1ll << 32) ||
+      (int64_t)num_scenes * b->T_max * b->K_glob >= (1ll << 31)) {
     delete b;
-    return bfail(LFD_ERR_CAPACITY, "global tile and cluster bits exceed 32");
+    return bfail(LFD_ERR_CAPACITY, "tile, scene and cluster bits exceed 32");
   }
   for (int s = 0; s < num_scenes; ++s) {
-    b->g[s].bit_k = b->bit_k;
+    b->g[s].bit_k = b->bit_s + b->bit_kc;
     b->g[s].bit_t = b->bit_t;
+    b->g[s].key_code = (uint32_t)s << b->bit_kc;
   }
   cudaError_t e = b->small.ensure(4 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(b->small.p, 0, 4 * sizeof(unsigned long long));
@@ -205,7 +209,7 @@ int lfd_batch_reserve(lfd_batch* b, const int64_t* max_gaussians, int64_t max_pa
   const size_t st = radix_temp_bytes(items) > radix_temp_bytes(max_pairs) ? radix_temp_bytes(items)
                                                                          : radix_temp_bytes(max_pairs);
   B_CUDA(b->radix_tmp.ensure(st));
-  B_CUDA(b->ranges.ensure((size_t)b->T_total * b->K_glob * sizeof(uint2)));
+  B_CUDA(b->ranges.ensure((size_t)b->n * b->T_max * b->K_glob * sizeof(uint2)));
   b->cap_items = items;
   b->cap_P = max_pairs;
   b->reserved = true;
@@ -273,20 +277,26 @@ int lfd_batch_render(lfd_batch* b, const lfd_gaussians* scenes, const lfd_camera
                                 b->pair_key[0].as<uint32_t>(), nullptr, b->pair_val[0].as<uint32_t>(),
                                 desc + (size_t)item_off[s] * kBinDescBytes, d_small, P, d_err, st));
   }
-  // one stable sort on the global tile bits: (global tile, cluster, depth)
+  // one stable sort on the tile bits: (tile, scene, cluster, depth)
   alt = false;
+  const int low = b->bit_s + b->bit_kc;
   B_CUDA(radix_sort_u32(b->pair_key[0].as<uint32_t>(), b->pair_key[1].as<uint32_t>(),
                         b->pair_val[0].as<uint32_t>(), b->pair_val[1].as<uint32_t>(), (int64_t)P,
-                        d_small, b->bit_k, b->bit_k + b->bit_t, b->radix_tmp.p, &alt, d_err, st));
+                        d_small, low, low + b->bit_t, b->radix_tmp.p, &alt, d_err, st));
   const int kb = alt ? 1 : 0;
-  PanelGeom gr = b->g[0];
-  gr.T = b->T_total;
-  gr.K = b->K_glob;
-  gr.bit_k = b->bit_k;
-  gr.bit_t = b->bit_t;
-  gr.tile_base = 0;
-  B_CUDA(launch_ranges(gr, (int64_t)P, d_small, b->pair_key[kb].as<uint32_t>(), nullptr,
-                       b->ranges.as<uint2>(), st));
+  BatchRangeArgs ra;
+  memset(&ra, 0, sizeof(ra));
+  ra.n_scenes = b->n;
+  ra.T_max = b->T_max;
+  ra.K_glob = b->K_glob;
+  ra.bit_k = low;
+  ra.bit_kc = b->bit_kc;
+  for (int s = 0; s < b->n; ++s) {
+    ra.T[s] = b->g[s].T;
+    ra.K[s] = b->g[s].K;
+  }
+  B_CUDA(launch_ranges_batch(ra, (int64_t)P, d_small, b->pair_key[kb].as<uint32_t>(),
+                             b->ranges.as<uint2>(), st));
   // one persistent blend over every scene's runs
   BatchBlendArgs ba;
   memset(&ba, 0, sizeof(ba));
@@ -313,6 +323,7 @@ int lfd_batch_render(lfd_batch* b, const lfd_gaussians* scenes, const lfd_camera
   ba.n_scenes = b->n;
   ba.total_runs = b->run_base[b->n];
   ba.K_glob = b->K_glob;
+  ba.T_max = b->T_max;
   ba.ranges = b->ranges.as<uint2>();
   ba.work = b->work.as<unsigned int>();
   ba.P_dev = d_small;

@@ -465,8 +465,8 @@ __global__ void __launch_bounds__(32 * kEmitWarps)
     BinQ q;
     if (bin_prep(co.x, co.y, co.z, color_tau[r].w, q))
       bin_union(g, q, means2d + (size_t)r * g.C, [&](int t) {
-        const uint32_t tg = (uint32_t)(t + g.tile_base);
-        kdst[p] = kWide ? (KeyT)(((uint64_t)tg << shift) | lo) : (KeyT)((tg << shift) | k);
+        kdst[p] = kWide ? (KeyT)(((uint64_t)t << shift) | lo)
+                        : (KeyT)(((uint32_t)t << shift) | g.key_code | k);
         vdst[p] = i;
         ++p;
       });
@@ -509,8 +509,8 @@ __global__ void __launch_bounds__(32 * kEmitWarps)
       while (mask) {
         const int bit = __ffsll((long long)mask) - 1;
         mask &= mask - 1ull;
-        const uint32_t t = (uint32_t)((ty0 + rr) * g.TX + c0 + bit + g.tile_base);
-        kdst[p] = kWide ? (KeyT)(((uint64_t)t << shift) | lo) : (KeyT)((t << shift) | k);
+        const uint32_t t = (uint32_t)((ty0 + rr) * g.TX + c0 + bit);
+        kdst[p] = kWide ? (KeyT)(((uint64_t)t << shift) | lo) : (KeyT)((t << shift) | g.key_code | k);
         vdst[p] = i;
         ++p;
       }
@@ -556,6 +556,38 @@ __global__ void k_ranges(PanelGeom g, int64_t P_cap, const unsigned long long* _
   while (lo2 < hi) {
     const int64_t mid = (lo2 + hi) >> 1;
     if (tk_at(mid) <= target) lo2 = mid + 1;
+    else hi = mid;
+  }
+  ranges[q] = lo2 > lo ? make_uint2((uint32_t)lo, (uint32_t)lo2) : make_uint2(0u, 0u);
+}
+
+// Batched range table: one thread per (scene, tile, cluster).
+__global__ void k_ranges_batch(BatchRangeArgs ra, int64_t P_cap, const unsigned long long* __restrict__ P_dev,
+                               const uint32_t* __restrict__ keys32, uint2* __restrict__ ranges) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t per_scene = (int64_t)ra.T_max * ra.K_glob;
+  if (q >= per_scene * ra.n_scenes) return;
+  const int sc = (int)(q / per_scene);
+  const int64_t rem = q - (int64_t)sc * per_scene;
+  const int t = (int)(rem / ra.K_glob), k = (int)(rem - (int64_t)t * ra.K_glob);
+  if (t >= ra.T[sc] || k >= ra.K[sc]) {
+    ranges[q] = make_uint2(0u, 0u);
+    return;
+  }
+  int64_t P = P_cap;
+  if (P_dev && *P_dev < (unsigned long long)P_cap) P = (int64_t)*P_dev;
+  const uint32_t target = ((uint32_t)t << ra.bit_k) | ((uint32_t)sc << ra.bit_kc) | (uint32_t)k;
+  int64_t lo = 0, hi = P;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (keys32[mid] < target) lo = mid + 1;
+    else hi = mid;
+  }
+  int64_t lo2 = lo;
+  hi = P;
+  while (lo2 < hi) {
+    const int64_t mid = (lo2 + hi) >> 1;
+    if (keys32[mid] <= target) lo2 = mid + 1;
     else hi = mid;
   }
   ranges[q] = lo2 > lo ? make_uint2((uint32_t)lo, (uint32_t)lo2) : make_uint2(0u, 0u);
@@ -649,6 +681,15 @@ cudaError_t launch_ranges(const PanelGeom& g, int64_t P, const unsigned long lon
   const int64_t runs = (int64_t)g.T * g.K;
   if (runs == 0) return cudaSuccess;
   k_ranges<<<blocks_for(runs, 256), 256, 0, s>>>(g, P, P_dev, keys32, keys64, ranges);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ranges_batch(const BatchRangeArgs& r, int64_t P, const unsigned long long* P_dev,
+                                const uint32_t* keys32, uint2* ranges, cudaStream_t s) {
+  const int64_t n = (int64_t)r.n_scenes * r.T_max * r.K_glob;
+  if (n == 0) return cudaSuccess;
+  k_ranges_batch<<<blocks_for(n, 256), 256, 0, s>>>(r, P, P_dev, keys32, ranges);
   note_launches(1);
   return cudaGetLastError();
 }

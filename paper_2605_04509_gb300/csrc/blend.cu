@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(256) k_blend_batch(BatchBlendArgs b) {
     const uint32_t local = r - sc.run_base;
     const int k = (int)(local / (uint32_t)sc.g.T);
     const int t = (int)(local - (uint32_t)k * (uint32_t)sc.g.T);
-    const uint2 rg = b.ranges[(size_t)(sc.g.tile_base + t) * b.K_glob + k];
+    const uint2 rg = b.ranges[((size_t)si * b.T_max + t) * b.K_glob + k];
     blend_run<R, false>(sc.g, sc.a, k, t, rg, smem);
   }
 }

@@ -26,10 +26,10 @@ struct PanelGeom {
   int TW, TH, TX, TY, T;
   int cap;  // 3 * TW * TH
   int bit_k, bit_t;
-  // Offsets of this panel's tiles and clusters in a batch's global tile and
-  // cluster numbering (0 for a single scene): pair keys carry the global
-  // tile, item keys the global cluster.
-  int tile_base = 0;
+  // Batched scenes: the pair key is (t << bit_k) | key_code | k, where
+  // key_code carries the scene's index above its cluster bits (0 for a
+  // single scene), and item keys carry the global cluster cluster_base + k.
+  uint32_t key_code = 0;
   int cluster_base = 0;
 };
 
@@ -94,6 +94,15 @@ cudaError_t launch_gather_u32(const uint32_t* src, const uint32_t* idx, int64_t 
 cudaError_t launch_ranges(const PanelGeom& g, int64_t P, const unsigned long long* P_dev,
                           const uint32_t* keys32, const uint64_t* keys64, uint2* ranges,
                           cudaStream_t s);
+// Range table of a batch: [scene][T_max][K_glob]; the run of (s, t, k) has
+// key (t << bit_k) | (s << bit_kc) | k. Entries with t >= T[s] or k >= K[s]
+// are (0, 0).
+struct BatchRangeArgs {
+  int n_scenes, T_max, K_glob, bit_k, bit_kc;
+  int T[16], K[16];
+};
+cudaError_t launch_ranges_batch(const BatchRangeArgs& r, int64_t P, const unsigned long long* P_dev,
+                                const uint32_t* keys32, uint2* ranges, cudaStream_t s);
 
 // ---- scan and radix sort (sort.cu) ----
 size_t scan_temp_bytes(int64_t n);
@@ -116,6 +125,69 @@ cudaError_t radix_sort_u64(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals,
                            uint32_t* vals_alt, int64_t n, const unsigned long long* n_dev,
                            int begin_bit, int end_bit, void* temp, bool* result_in_alt,
                            uint32_t* err, cudaStream_t s);
+
+// ---- bulk-copy and mbarrier helpers (inline PTX) ----
+constexpr int kSpinLimit = 1 << 22;                   // polls of an mbarrier before giving up
+constexpr unsigned long long kWaitNs = 250000000ull;  // or 0.25 s, whichever comes first
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// global -> shared bulk copy (both 16-byte aligned, bytes a multiple of 16),
+// completion counted on the mbarrier
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait for one phase of an mbarrier: false once kWaitNs nanoseconds
+// have passed (or kSpinLimit polls, whichever comes first).
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, uint32_t parity) {
+  const unsigned long long t0 = global_ns();
+  for (int i = 0; i < kSpinLimit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 15) == 15 && global_ns() - t0 > kWaitNs) return false;
+    if (i > 16) __nanosleep(32);
+  }
+  return false;
+}
 
 // ---- blend (blend.cu) ----
 // 2^x on the special-function unit (hand-written PTX instruction).
@@ -156,7 +228,7 @@ cudaError_t launch_blend(const PanelGeom& g, const BlendArgs& a, cudaStream_t s)
 // and image) in one persistent launch over all their (cluster, tile) runs.
 constexpr int kMaxBatchScenes = 16;
 struct SceneBlend {
-  PanelGeom g;        // tile_base: first global tile of the scene
+  PanelGeom g;        // key_code: the scene's index in the pair keys
   BlendArgs a;        // the scene's tables, attributes and image
   uint32_t run_base;  // first global run (runs of a scene are k * T + t)
 };
@@ -164,8 +236,9 @@ struct BatchBlendArgs {
   SceneBlend sc[kMaxBatchScenes];
   int n_scenes;
   uint32_t total_runs;
-  int K_glob;            // clusters per tile in the global range table
-  const uint2* ranges;   // [global tiles][K_glob]
+  int K_glob;            // clusters per (scene, tile) in the range table
+  int T_max;             // tiles per scene in the range table
+  const uint2* ranges;   // [scene][T_max][K_glob]
   unsigned int* work;    // work counter (zeroed by the launcher)
   const unsigned long long* P_dev;
   unsigned long long P_cap;

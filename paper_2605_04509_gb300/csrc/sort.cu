@@ -121,12 +121,11 @@ __global__ void __launch_bounds__(kScanThreads)
 
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
-constexpr int kSortThreads = 256;
+constexpr int kSortThreads = 512;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortRounds = 16;
+constexpr int kSortRounds = 8;
 constexpr int kSortTile = kSortThreads * kSortRounds;  // 4096 items
-constexpr int kSpinLimit = 1 << 22;                   // polls of an mbarrier before giving up
-constexpr unsigned long long kWaitNs = 250000000ull;  // or 0.25 s, whichever comes first
+static_assert(kSortThreads >= kRadix, "one thread per digit in the digit phases");
 
 template <typename K>
 __device__ __forceinline__ int digit_of(K key, int shift, int mask) {
@@ -181,10 +180,12 @@ __global__ void __launch_bounds__(kSortThreads)
   }
   __syncthreads();
   const int d = threadIdx.x;
-  uint32_t sum = 0;
+  if (d < kRadix) {
+    uint32_t sum = 0;
 #pragma unroll
-  for (int w = 0; w < kSortWarps; ++w) sum += s_h[w][d];
-  hist[(int64_t)d * nb + blockIdx.x] = sum;
+    for (int w = 0; w < kSortWarps; ++w) sum += s_h[w][d];
+    hist[(int64_t)d * nb + blockIdx.x] = sum;
+  }
 }
 
 // Peer mask of the lanes holding the same digit, from one ballot per digit
@@ -201,62 +202,6 @@ __device__ __forceinline__ unsigned digit_peers(int d, bool valid) {
   return m;
 }
 
-// ---- bulk-copy and mbarrier helpers (inline PTX) ----
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
-  uint32_t done;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(done)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-
-// global -> shared bulk copy (both 16-byte aligned, bytes a multiple of 16),
-// completion counted on the mbarrier
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
-                                         unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Bounded wait for one phase of an mbarrier: false once kWaitNs nanoseconds
-// have passed (or kSpinLimit polls, whichever comes first).
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, uint32_t parity) {
-  const unsigned long long t0 = global_ns();
-  for (int i = 0; i < kSpinLimit; ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 15) == 15 && global_ns() - t0 > kWaitNs) return false;
-    if (i > 16) __nanosleep(32);
-  }
-  return false;
-}
-
 // Stable scatter of one pass. Block b handles tiles b, b + G, b + 2G, ...
 // (G = gridDim.x); tile t's output base per digit is hscan[d * nb + t].
 template <typename K>
@@ -265,7 +210,6 @@ __global__ void __launch_bounds__(kSortThreads)
                   uint32_t* __restrict__ vout, int64_t n_cap, const unsigned long long* __restrict__ n_dev,
                   int shift, int mask, const uint32_t* __restrict__ hscan, int64_t nb,
                   uint32_t* __restrict__ err) {
-  static_assert(kRadix == kSortThreads, "one digit per thread");
   extern __shared__ __align__(128) unsigned char s_raw[];
   // [in0 keys][in0 vals][in1 keys][in1 vals][out keys][out vals]
   constexpr size_t kBuf = (size_t)kSortTile * (sizeof(K) + sizeof(uint32_t));
@@ -275,10 +219,11 @@ __global__ void __launch_bounds__(kSortThreads)
   };
   K* s_key = reinterpret_cast<K*>(s_raw + 2 * kBuf);
   uint32_t* s_val = reinterpret_cast<uint32_t*>(s_key + kSortTile);
-  __shared__ uint32_t s_wcnt[kSortWarps][kRadix];
+  // per-warp digit counters (at most 4096 per tile: 16 bits suffice)
+  __shared__ uint16_t s_wcnt[kSortWarps][kRadix];
   __shared__ uint32_t s_base[kRadix];
   __shared__ uint32_t s_dstart[kRadix];
-  __shared__ uint32_t s_wsum[kSortWarps];
+  __shared__ uint32_t s_wsum[kRadix / 32];
   __shared__ __align__(8) unsigned long long s_bar[2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
@@ -313,7 +258,7 @@ __global__ void __launch_bounds__(kSortThreads)
     const int64_t tile0 = tile * kSortTile;
     const int cnt = (int)min((int64_t)kSortTile, n - tile0);
     for (int a = threadIdx.x; a < kSortWarps * kRadix; a += kSortThreads) (&s_wcnt[0][0])[a] = 0;
-    s_base[d] = hscan[(int64_t)d * nb + tile];
+    if (d < kRadix) s_base[d] = hscan[(int64_t)d * nb + tile];
     if (threadIdx.x == 0) fetch(b ^ 1, tile + gridDim.x);
     if (is_full(tile)) {
       const uint32_t ph = (parity >> b) & 1u;
@@ -344,30 +289,34 @@ __global__ void __launch_bounds__(kSortThreads)
       const unsigned peers = digit_peers(dd, valid);
       const int rank = __popc(peers & lt);
       const int pc = __popc(peers);
-      const uint32_t bw = valid ? s_wcnt[warp][dd] : 0u;
+      const uint32_t bw = valid ? (uint32_t)s_wcnt[warp][dd] : 0u;
       __syncwarp();
-      if (valid && rank == pc - 1) s_wcnt[warp][dd] = bw + (uint32_t)pc;
+      if (valid && rank == pc - 1) s_wcnt[warp][dd] = (uint16_t)(bw + (uint32_t)pc);
       __syncwarp();
       rk[r] = bw + (uint32_t)rank;
       dg[r] = dd;
     }
     __syncthreads();
-    uint32_t run = 0;
+    // digit phase (threads 0..255, one per digit): exclusive prefix of the
+    // warp counters, then the tile's digit starts
+    uint32_t run = 0, x = 0;
+    if (d < kRadix) {
 #pragma unroll
-    for (int w = 0; w < kSortWarps; ++w) {
-      const uint32_t c = s_wcnt[w][d];
-      s_wcnt[w][d] = run;
-      run += c;
-    }
-    {
-      uint32_t x = run;
+      for (int w = 0; w < kSortWarps; ++w) {
+        const uint32_t c = s_wcnt[w][d];
+        s_wcnt[w][d] = (uint16_t)run;
+        run += c;
+      }
+      x = run;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
       }
       if (lane == 31) s_wsum[warp] = x;
-      __syncthreads();
+    }
+    __syncthreads();
+    if (d < kRadix) {
       uint32_t pre = 0;
       for (int w = 0; w < warp; ++w) pre += s_wsum[w];
       s_dstart[d] = pre + x - run;
