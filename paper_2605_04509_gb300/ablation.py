@@ -2,7 +2,7 @@
 stage breakdown of T5/T6): cross-view attribute reuse on/off (clusters of 8
 views vs 1) and view-coherent remapping on/off, on one synthetic workload.
 
-    python -m paper_2605_04509_gb300.ablation [--workload paper4k] [--frames 20]
+    python -m paper_2605_04509_gb300.ablation [--workload paper4k] [--frames 20] [--tile 32x16]
 
 Prints one JSON line per configuration and a markdown table. Every
 configuration renders through the C ABI; the images of the remap on/off pairs
@@ -17,7 +17,7 @@ import json
 import numpy as np
 
 
-def run(workload: str = "paper4k", frames: int = 20, warmup: int = 3):
+def run(workload: str = "paper4k", frames: int = 20, warmup: int = 3, tile=(32, 16)):
     import torch
 
     from . import lfd, synth
@@ -30,7 +30,7 @@ def run(workload: str = "paper4k", frames: int = 20, warmup: int = 3):
     rows = []
     for c, remap, name in ((1, False, "w/o reuse, w/o remap"), (1, True, "w/o reuse"),
                            (8, False, "w/o remap"), (8, True, "ours")):
-        plan = lfd.Plan(w.panel, views_per_cluster=c, remap=remap)
+        plan = lfd.Plan(w.panel, tile=tuple(tile), views_per_cluster=c, remap=remap)
         for _ in range(warmup):
             plan.render(s, cams, out)
         plan.set_flags(lfd.FLAG_COUNT_EVALS)
@@ -47,7 +47,8 @@ def run(workload: str = "paper4k", frames: int = 20, warmup: int = 3):
         torch.cuda.synchronize()
         tot = plan.stage_totals(reset=True)
         ms = e0.elapsed_time(e1) / frames
-        row = {"config": name, "views_per_cluster": c, "remap": remap, "fps": 1000.0 / ms,
+        row = {"config": name, "views_per_cluster": c, "remap": remap, "tile": list(tile),
+               "fps": 1000.0 / ms,
                "ms_per_frame": ms, "pairs": st["num_pairs"], "visits": st["num_visits"],
                "evals": st["num_evals"],
                "image_sha256": hashlib.sha256(out.cpu().numpy().tobytes()).hexdigest()[:16]}
@@ -71,9 +72,10 @@ def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--workload", default="paper4k")
     ap.add_argument("--frames", type=int, default=20)
+    ap.add_argument("--tile", default="32x16")
     args = ap.parse_args()
     np.set_printoptions(precision=3)
-    run(args.workload, args.frames)
+    run(args.workload, args.frames, tile=tuple(int(v) for v in args.tile.split("x")))
 
 
 if __name__ == "__main__":

@@ -4,6 +4,10 @@ uniform), panels assigned round-robin from 1536x2048 / 48 views,
 3840x2160 / 45 views and 7680x4320 / 100 views, all attributes in FP16.
 
     python -m paper_2605_04509_gb300.batching [--frames 3] [--scenes 16]
+    python -m paper_2605_04509_gb300.batching --probe --tiles 16x16,32x16,32x16
+
+(--probe: only the batch, with the given tile per panel and no tuning or
+single-scene frames, rendered --frames times; for profiler launch lists.)
 
 Per panel the autotuner picks the tile shape on that panel's first scene;
 the staging depth (subpixels per blend thread) is then tuned for the whole
@@ -196,12 +200,40 @@ def run(frames: int = 3, n_scenes: int = 16, tune_frames: int = 2):
     return line
 
 
+def probe(frames: int, n_scenes: int, tiles):
+    """Build the batch with fixed tiles (one per panel) and render it."""
+    import torch
+
+    from . import lfd
+
+    sizes = scene_sizes(n_scenes)
+    panel_of = [s % len(PANELS) for s in range(n_scenes)]
+    scenes = [lfd.scene_to_device(synth.mixture_scene(sizes[s], 100 + s), attr_dtype=torch.float16)
+              for s in range(n_scenes)]
+    cams = [synth.arc_cameras(PANELS[p][2], PANELS[p][1].width, PANELS[p][1].height)
+            for p in range(len(PANELS))]
+    plans = {p: lfd.Plan(PANELS[p][1], tile=tiles[p], views_per_cluster=8) for p in range(len(PANELS))}
+    batch = lfd.Batch([plans[panel_of[s]] for s in range(n_scenes)])
+    batch.reserve(sizes, MAX_PAIRS)
+    outs = batch.images()
+    for it in range(frames):
+        batch.render(scenes, [cams[panel_of[s]] for s in range(n_scenes)], outs)
+        print(json.dumps({"frame": it, "pairs": batch.status()}), flush=True)
+    batch.close()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--frames", type=int, default=3)
     ap.add_argument("--scenes", type=int, default=16)
+    ap.add_argument("--probe", action="store_true")
+    ap.add_argument("--tiles", default="16x16,32x16,32x16")
     args = ap.parse_args()
-    run(args.frames, args.scenes)
+    if args.probe:
+        tiles = [tuple(int(v) for v in t.split("x")) for t in args.tiles.split(",")]
+        probe(args.frames, args.scenes, tiles)
+    else:
+        run(args.frames, args.scenes)
 
 
 if __name__ == "__main__":
