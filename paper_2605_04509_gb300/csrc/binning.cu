@@ -240,10 +240,10 @@ constexpr int kBinWarps = 4;
 // views over one tile row. Items whose union is wider than 64 tile columns
 // are walked by their own lane. Each item's per-view boxes (bin_view) are
 // computed once by its own lane and kept in shared memory for the units.
-struct BoxS {
-  float mx, my, bx0, bx1;
-  int y0, y1;  // y0 > y1: the view does not see the Gaussian
-};
+// Per-(item, view) boxes kept in shared memory field by field,
+// [field][view][item of the block], so that lanes reading different items'
+// boxes of one view hit consecutive words (no bank conflicts).
+constexpr int kBoxFields = 6;  // mx, my, bx0, bx1, y0, y1 (y0 > y1: not seen)
 
 __global__ void __launch_bounds__(32 * kBinWarps)
     k_bin_count(PanelGeom g, int64_t M, const float2* __restrict__ means2d,
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(32 * kBinWarps)
                 const uint32_t* __restrict__ order, int64_t n_items, uint32_t* __restrict__ counts,
                 BinDesc* __restrict__ desc) {
   __shared__ uint32_t s_n[kBinWarps][32];
-  extern __shared__ BoxS s_box[];  // [kBinWarps][32][C]
+  extern __shared__ float s_box[];  // [kBoxFields][C][32 * kBinWarps]
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool in = s < n_items;
@@ -259,7 +259,9 @@ __global__ void __launch_bounds__(32 * kBinWarps)
   BinQ q = {};
   bool ok = false;
   int ty0 = INT_MAX, ty1 = -1, c0 = INT_MAX, c1 = -1;
-  BoxS* my_box = s_box + (size_t)(warp * 32 + lane) * g.C;
+  constexpr int kItems = 32 * kBinWarps;
+  auto box = [&](int f, int l, int item) -> float& { return s_box[(f * g.C + l) * kItems + item]; };
+  const int my_item = warp * 32 + lane;
   if (in) {
     r = order ? order[s] : (uint32_t)s;
     const float4 co = conic_opacity[r];
@@ -272,14 +274,12 @@ __global__ void __launch_bounds__(32 * kBinWarps)
       const float2 m = mr[l];
       BinV v;
       bin_view(q, m.x, m.y, g.W, g.H, v);
-      BoxS b;
-      b.mx = v.mx;
-      b.my = v.my;
-      b.bx0 = v.bx0;
-      b.bx1 = v.bx1;
-      b.y0 = v.valid ? v.y0 : 1;
-      b.y1 = v.valid ? v.y1 : 0;
-      my_box[l] = b;
+      box(0, l, my_item) = v.mx;
+      box(1, l, my_item) = v.my;
+      box(2, l, my_item) = v.bx0;
+      box(3, l, my_item) = v.bx1;
+      box(4, l, my_item) = __int_as_float(v.valid ? v.y0 : 1);
+      box(5, l, my_item) = __int_as_float(v.valid ? v.y1 : 0);
       if (!v.valid) continue;
       ty0 = min(ty0, v.y0 / g.TH);
       ty1 = max(ty1, v.y1 / g.TH);
@@ -308,19 +308,18 @@ __global__ void __launch_bounds__(32 * kBinWarps)
     const int c0j = __shfl_sync(0xffffffffu, c0, j);
     const bool fitsj = __shfl_sync(0xffffffffu, fits, j);
     if (u < U) {
-      const BoxS* bj = s_box + (size_t)(warp * 32 + j) * g.C;
+      const int item_j = warp * 32 + j;
       const int ty = ty0j + rr;
       unsigned long long mask = 0ull;
       for (int l = 0; l < g.C; ++l) {
-        const BoxS bx = bj[l];
         BinV v;
-        v.mx = bx.mx;
-        v.my = bx.my;
-        v.bx0 = bx.bx0;
-        v.bx1 = bx.bx1;
-        v.y0 = bx.y0;
-        v.y1 = bx.y1;
-        v.valid = bx.y0 <= bx.y1;
+        v.mx = box(0, l, item_j);
+        v.my = box(1, l, item_j);
+        v.bx0 = box(2, l, item_j);
+        v.bx1 = box(3, l, item_j);
+        v.y0 = __float_as_int(box(4, l, item_j));
+        v.y1 = __float_as_int(box(5, l, item_j));
+        v.valid = v.y0 <= v.y1;
         int a, bb;
         if (!bin_row(qj, v, ty, g.TW, g.TH, a, bb)) continue;
         const int len = bb - a + 1;
@@ -614,7 +613,7 @@ cudaError_t launch_bin_count(const PanelGeom& g, int64_t M, const float* means2d
                              const uint32_t* order, int64_t n_items, uint32_t* counts, void* desc,
                              cudaStream_t s) {
   if (n_items == 0) return cudaSuccess;
-  const size_t smem = (size_t)kBinWarps * 32 * g.C * sizeof(BoxS);
+  const size_t smem = (size_t)kBoxFields * g.C * 32 * kBinWarps * sizeof(float);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
