@@ -79,7 +79,7 @@ __device__ __forceinline__ void bin_view(const BinQ& g, float mx, float my, int 
 }
 
 // tile-column interval [tx0, tx1] of view v in tile row ty
-__device__ __forceinline__ bool bin_row(const BinQ& g, const BinV& v, int ty, int TW, int TH,
+__device__ __forceinline__ bool bin_row(const BinQ& g, const BinV& v, int ty, int TH, uint32_t tw_magic,
                                         int& tx0, int& tx1) {
   if (!v.valid) return false;
   const int ya = max(ty * TH, v.y0);
@@ -99,8 +99,8 @@ __device__ __forceinline__ bool bin_row(const BinQ& g, const BinV& v, int ty, in
   const float fx0 = fmaxf(ceilf(__fsub_rn(xL, 0.5f)), v.bx0);
   const float fx1 = fminf(floorf(__fsub_rn(xR, 0.5f)), v.bx1);
   if (!(fx0 <= fx1)) return false;
-  tx0 = (int)fx0 / TW;
-  tx1 = (int)fx1 / TW;
+  tx0 = (int)__umulhi((unsigned)(int)fx0, tw_magic);
+  tx1 = (int)__umulhi((unsigned)(int)fx1, tw_magic);
   return true;
 }
 
@@ -117,10 +117,10 @@ __device__ __forceinline__ void bin_extent(const PanelGeom& pg, const BinQ& q,
     BinV v;
     bin_view(q, m.x, m.y, pg.W, pg.H, v);
     if (!v.valid) continue;
-    ty0 = min(ty0, v.y0 / pg.TH);
-    ty1 = max(ty1, v.y1 / pg.TH);
-    c0 = min(c0, (int)v.bx0 / pg.TW);
-    c1 = max(c1, (int)v.bx1 / pg.TW);
+    ty0 = min(ty0, (int)__umulhi((unsigned)v.y0, pg.th_magic));
+    ty1 = max(ty1, (int)__umulhi((unsigned)v.y1, pg.th_magic));
+    c0 = min(c0, (int)__umulhi((unsigned)(int)v.bx0, pg.tw_magic));
+    c1 = max(c1, (int)__umulhi((unsigned)(int)v.bx1, pg.tw_magic));
   }
 }
 
@@ -140,7 +140,7 @@ __device__ __forceinline__ uint32_t bin_rows(const PanelGeom& pg, const BinQ& q,
         BinV v;
         bin_view(q, m.x, m.y, pg.W, pg.H, v);
         int a, b;
-        if (!bin_row(q, v, ty, pg.TW, pg.TH, a, b)) continue;
+        if (!bin_row(q, v, ty, pg.TH, pg.tw_magic, a, b)) continue;
         a = max(a, w0);
         b = min(b, w0 + 63);
         if (a > b) continue;
@@ -186,7 +186,7 @@ __global__ void k_item_keys(PanelGeom g, int64_t M, const float* __restrict__ de
                             uint32_t* __restrict__ vals) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= (int64_t)g.K * M) return;
-  const uint64_t k = (uint64_t)(r / M);
+  const uint64_t k = (uint64_t)((uint32_t)r / (uint32_t)M);  // K M < 2^32
   const float tau = color_tau[r].w;
   const uint32_t d = tau >= 0.f ? __float_as_uint(depth[r]) : 0xffffffffu;
   keys[r] = ((k + (uint64_t)g.cluster_base) << 32) | d;
@@ -281,10 +281,10 @@ __global__ void __launch_bounds__(32 * kBinWarps)
       box(4, l, my_item) = __int_as_float(v.valid ? v.y0 : 1);
       box(5, l, my_item) = __int_as_float(v.valid ? v.y1 : 0);
       if (!v.valid) continue;
-      ty0 = min(ty0, v.y0 / g.TH);
-      ty1 = max(ty1, v.y1 / g.TH);
-      c0 = min(c0, (int)v.bx0 / g.TW);
-      c1 = max(c1, (int)v.bx1 / g.TW);
+      ty0 = min(ty0, (int)__umulhi((unsigned)v.y0, g.th_magic));
+      ty1 = max(ty1, (int)__umulhi((unsigned)v.y1, g.th_magic));
+      c0 = min(c0, (int)__umulhi((unsigned)(int)v.bx0, g.tw_magic));
+      c1 = max(c1, (int)__umulhi((unsigned)(int)v.bx1, g.tw_magic));
     }
   }
   const int rows = ok && ty1 >= ty0 ? ty1 - ty0 + 1 : 0;
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(32 * kBinWarps)
         v.y1 = __float_as_int(box(5, l, item_j));
         v.valid = v.y0 <= v.y1;
         int a, bb;
-        if (!bin_row(qj, v, ty, g.TW, g.TH, a, bb)) continue;
+        if (!bin_row(qj, v, ty, g.TH, g.tw_magic, a, bb)) continue;
         const int len = bb - a + 1;
         const unsigned long long bits = len == 64 ? ~0ull : ((1ull << len) - 1ull);
         mask |= bits << (a - c0j);
@@ -351,7 +351,7 @@ __global__ void k_bin_emit(PanelGeom g, int64_t M, const float2* __restrict__ me
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n_items) return;
   const uint32_t r = order ? order[s] : (uint32_t)s;
-  const uint32_t k = (uint32_t)(r / M);
+  const uint32_t k = r / (uint32_t)M;
   const uint32_t i = (uint32_t)(r - (uint64_t)k * M);
   uint32_t pos = offsets[s];
   if (desc) {
@@ -456,7 +456,7 @@ __global__ void __launch_bounds__(32 * kEmitWarps)
   // unions that did not fit a descriptor: the owner lane redoes the geometry
   const bool redo = in && n && ((h >> 40) & 1ull);
   if (redo) {
-    const uint32_t k = (uint32_t)(r / M);
+    const uint32_t k = r / (uint32_t)M;  // K M < 2^32
     const uint32_t i = (uint32_t)(r - (uint64_t)k * M);
     const uint64_t lo = kWide ? (((uint64_t)k << 32) | __float_as_uint(depth[r])) : 0ull;
     uint32_t p = pos - shift_out;
@@ -498,7 +498,7 @@ __global__ void __launch_bounds__(32 * kEmitWarps)
         __shfl_sync(0xffffffffu, (uint32_t)h, j);
     if (u < U) {
       const int ty0 = (int)(hj & 0xffffull), c0 = (int)((hj >> 16) & 0xffffull);
-      const uint32_t k = (uint32_t)(rj / M);
+      const uint32_t k = rj / (uint32_t)M;
       const uint32_t i = (uint32_t)(rj - (uint64_t)k * M);
       const uint64_t lo = kWide ? (((uint64_t)k << 32) | __float_as_uint(depth[rj])) : 0ull;
       uint32_t p = pj - shift_out;

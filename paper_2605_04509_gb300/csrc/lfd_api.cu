@@ -280,6 +280,8 @@ int lfd_plan_create(const lfd_panel* panel, const lfd_opts* opts, lfd_plan** out
   g.TY = (g.H + g.TH - 1) / g.TH;
   g.T = g.TX * g.TY;
   g.cap = 3 * g.TW * g.TH;
+  g.tw_magic = div_magic(g.TW);
+  g.th_magic = div_magic(g.TH);
   g.bit_k = ceil_log2((uint64_t)g.K);
   g.bit_t = ceil_log2((uint64_t)g.T);
   if (g.bit_t + g.bit_k > 32) {

@@ -31,7 +31,11 @@ struct PanelGeom {
   // single scene), and item keys carry the global cluster cluster_base + k.
   uint32_t key_code = 0;
   int cluster_base = 0;
+  // floor(x / TW) and floor(x / TH) for 0 <= x < 2^16 as __umulhi(x, magic)
+  // with magic = floor(2^32 / d) + 1 (exact there, since d <= 64)
+  uint32_t tw_magic = 0, th_magic = 0;
 };
+inline uint32_t div_magic(int d) { return (uint32_t)((1ull << 32) / (unsigned)d + 1ull); }
 
 // ---- plan tables (plan_kernels.cu) ----
 cudaError_t launch_view_index(int W, int H, int N, double tan_slant, double pitch,
