@@ -203,3 +203,39 @@ def test_bounded_wait_gives_up_and_reports():
     # the context is still usable
     x = torch.ones(10, device="cuda")
     assert float(x.sum()) == 10.0
+
+
+def test_batch_with_an_empty_scene_and_one_scene_batches():
+    plans, scenes, cams, refs, Ps = batch_case()
+    # a scene without Gaussians renders the background only
+    host0 = synth.uniform_scene(1, 103)
+    host0 = {k: v[:0] for k, v in host0.items()}
+    empty = lfd.scene_to_device(host0)
+    batch = lfd.Batch([plans[0], plans[1]])
+    batch.reserve([0, scenes[1]["means"].shape[0]], Ps[1] + 10)
+    outs = batch.render([empty, scenes[1]], [cams[0], cams[1]])
+    assert batch.status() == Ps[1]
+    assert torch.equal(outs[1], refs[1])
+    assert torch.all(outs[0] == 0.0)  # plan 0 has a black background
+    batch.close()
+    # a batch of one scene equals the single-scene frame
+    one = lfd.Batch([plans[1]])
+    one.reserve([scenes[1]["means"].shape[0]], Ps[1])
+    out = one.render([scenes[1]], [cams[1]])
+    assert one.status() == Ps[1]
+    assert torch.equal(out[0], refs[1])
+    one.close()
+
+
+def test_capacity_mode_with_no_gaussians():
+    w = synth.WORKLOADS["tiny"]
+    host = {k: v[:0] for k, v in synth.scene_for(w).items()}
+    scene = lfd.scene_to_device(host)
+    cams = synth.arc_cameras(w.rig, w.panel.width, w.panel.height)
+    plan = lfd.Plan(w.panel, views_per_cluster=8, bg=(0.25, 0.5, 0.75))
+    plan.reserve(10, 100)
+    out, _ = plan.render(scene, cams)
+    assert plan.status() == 0
+    img = out.cpu().numpy()
+    assert np.all(img[..., 0] == np.float32(0.25)) and np.all(img[..., 2] == np.float32(0.75))
+    plan.close()
