@@ -91,6 +91,10 @@ extern "C" {
 /* lfd_set_flags() bits */
 #define LFD_FLAG_STAGE_TIMING 1 /* fill lfd_stats.ms_* (adds host syncs)  */
 #define LFD_FLAG_COUNT_EVALS 2  /* fill lfd_stats.num_visits, num_evals  */
+/* Remapped lfd_render frames keep, per subpixel, where its walk stopped and
+ * its final transmittance (8 bytes per subpixel, allocated by lfd_set_flags);
+ * lfd_render_backward then starts from them instead of re-blending. */
+#define LFD_FLAG_KEEP_BLEND_STATE 4
 
 typedef struct lfd_plan lfd_plan;
 
@@ -212,9 +216,10 @@ LFD_API int lfd_render(lfd_plan *plan, const lfd_gaussians *g, const lfd_camera 
  * Gaussians and cameras, writes dL/d(means, scales, quats, opacities, sh)
  * into caller-owned FP32 device arrays shaped like the inputs (overwritten).
  * The blend gradient is taken through Eq. 9-10 with the 3DGS rules; each
- * subpixel re-blends its list to find its final transmittance and where it
- * stopped (no per-subpixel state is kept by the forward), then walks back to
- * front. The projection gradient follows Eq. 5-6: every view's 2D mean, and
+ * subpixel takes its final transmittance and the position where its walk
+ * stopped from the forward frame when that frame kept them
+ * (LFD_FLAG_KEEP_BLEND_STATE), else re-blends its list to find them, then
+ * walks back to front. The projection gradient follows Eq. 5-6: every view's 2D mean, and
  * the representative view's covariance (with the Jacobian's dependence on the
  * mean and the 1.3 tan(fov/2) clamp), conic inverse and SH colour (including
  * its view direction). Needs FP32 attributes and the remapped blend;

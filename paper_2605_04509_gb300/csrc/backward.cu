@@ -16,19 +16,57 @@ constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTMin = 1e-4f;
 
+// Sum 16 values over a warp in 16 shuffles: each butterfly stage trades half
+// of the values still held with the partner lane, so lane l ends with the
+// full sum of v[l >> 1] (v is overwritten). All 32 lanes must call it.
+__device__ __forceinline__ float warp_transpose_sum16(float (&v)[16], int lane) {
+  const unsigned full = 0xffffffffu;
+#pragma unroll
+  for (int half = 8, off = 16; half >= 1; half >>= 1, off >>= 1) {
+    const bool up = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const float send = up ? v[i] : v[i + half];
+      const float keep = up ? v[i + half] : v[i];
+      v[i] = keep + __shfl_xor_sync(full, send, off);
+    }
+  }
+  return v[0] + __shfl_xor_sync(full, v[0], 1);
+}
+
 // ---------------------------------------------------------------------------
 // blend backward: one CTA per (tile, cluster) run of Psi, one subpixel per
-// thread; the list is staged in shared memory batch by batch, first front to
-// back (forward replay), then from the last needed batch back to the first.
+// thread. Each subpixel needs its final transmittance and the list position
+// where its walk stopped: KEPT reads them from the forward frame, otherwise
+// the list is re-blended front to back (the forward blend's arithmetic,
+// staged batch by batch in shared memory). The list is then staged again
+// from the last needed batch back to the first and walked back to front.
+// As in the forward blend, each staged entry gets a bit per cluster view
+// telling whether that view's region (bounding box, one pixel of margin)
+// meets the tile; a subpixel only evaluates entries with its view's bit (the
+// others have alpha < 1/255 there). Psi lists a run's subpixels view by
+// view, so a warp holds one or two views: it walks the entries seen by any
+// of them, all lanes on the same entry, and sums each entry's gradients over
+// the warp (16-value transpose reduction) into shared memory; a batch's sums
+// go to global memory once per entry, by the thread that staged the entry.
 // ---------------------------------------------------------------------------
+template <bool KEPT>
 __global__ void __launch_bounds__(256) k_blend_backward(PanelGeom g, BlendArgs a, BlendGrads gr) {
   extern __shared__ float4 smem[];
   const int NB = blockDim.x;
+  const int NW = NB >> 5;
   const int C = g.C;
-  float4* s_co = smem;                                        // raw conic (a, b, c), opacity
-  float4* s_col = smem + NB;                                  // colour
-  float2* s_mean = reinterpret_cast<float2*>(smem + 2 * NB);  // [C][NB]
-  uint32_t* s_gid = reinterpret_cast<uint32_t*>(s_mean + C * NB);
+  float4* s_co = smem;                                          // raw conic (a, b, c), opacity
+  float4* s_col = smem + NB;                                    // colour
+  float4* s_gco = smem + 2 * NB;                                // d(a, b, c), d opacity
+  float4* s_gcol = smem + 3 * NB;                               // d colour
+  float2* s_mean = reinterpret_cast<float2*>(smem + 4 * NB);    // [C][NB]
+  float2* s_gmean = s_mean + C * NB;                            // [C][NB]
+  uint32_t* s_gid = reinterpret_cast<uint32_t*>(s_gmean + C * NB);
+  uint32_t* s_vm = s_gid + NB;                                  // view bits of each entry
+  uint16_t* s_idx = reinterpret_cast<uint16_t*>(s_vm + NB);     // [C][NB]
+  int* s_cnt = reinterpret_cast<int*>(s_idx + ((C * NB + 1) & ~1));  // [C][NW + 1]
+  __shared__ uint32_t s_last;
   const int k = blockIdx.x / g.T;
   const int t = blockIdx.x - k * g.T;
   const int s0 = a.seg[(size_t)t * (g.K + 1) + k];
@@ -37,157 +75,262 @@ __global__ void __launch_bounds__(256) k_blend_backward(PanelGeom g, BlendArgs a
   const uint2 rg = a.ranges[(size_t)t * g.K + k];
   if (rg.x == rg.y) return;
   const int tx = t % g.TX, ty = t / g.TX;
-  const int lane = threadIdx.x & 31;
-  __shared__ uint32_t s_last;
-  // runs longer than the block are processed in chunks of blockDim subpixels
-  for (int chunk = 0; chunk < n; chunk += NB) {
-  const int r = chunk + threadIdx.x;
-  bool act = r < n;
-  float px = 0.f, py = 0.f, G = 0.f;
-  int slot = 0, ch = 0;
-  if (act) {
-    const uint32_t e = a.psi[(size_t)t * g.cap + s0 + r];
-    const int view = (int)(e >> 16);
-    const int loc = (int)(e & 0xffffu);
-    const int xl = (loc / 3) % g.TW, yl = (loc / 3) / g.TW;
-    const int x = tx * g.TW + xl, y = ty * g.TH + yl;
-    ch = loc % 3;
-    px = (float)x + 0.5f;
-    py = (float)y + 0.5f;
-    slot = view - k * C;
-    G = gr.grad_out[((int64_t)y * g.W + x) * 3 + ch];
-  }
-  const bool live = act;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const float bx0 = (float)(tx * g.TW) + 0.5f - 1.f;
+  const float bx1 = (float)min(tx * g.TW + g.TW, g.W) - 0.5f + 1.f;
+  const float by0 = (float)(ty * g.TH) + 0.5f - 1.f;
+  const float by1 = (float)min(ty * g.TH + g.TH, g.H) - 0.5f + 1.f;
 
-  auto stage = [&](uint32_t base) {
+  // stage entry base + threadIdx.x: attributes, means and view bits; with
+  // compact, also list per view the staged entries with that view's bit.
+  // Called by every thread; it synchronises the block.
+  auto stage = [&](uint32_t base, bool compact) {
     const uint32_t e = base + threadIdx.x;
+    uint32_t mask = 0;
     if (e < rg.y) {
       const uint32_t gid = a.list[e];
       const size_t rec = (size_t)k * a.M + gid;
-      s_co[threadIdx.x] = reinterpret_cast<const float4*>(a.conic_opacity)[rec];
-      s_col[threadIdx.x] = reinterpret_cast<const float4*>(a.color_tau)[rec];
+      const float4 co = reinterpret_cast<const float4*>(a.conic_opacity)[rec];
+      const float4 ct = reinterpret_cast<const float4*>(a.color_tau)[rec];
+      s_co[threadIdx.x] = co;
+      s_col[threadIdx.x] = ct;
+      const float det = co.x * co.z - co.y * co.y;
+      const float hx = sqrtf(fmaxf(ct.w * co.z / det, 0.f));
+      const float hy = sqrtf(fmaxf(ct.w * co.x / det, 0.f));
       const float2* mp = reinterpret_cast<const float2*>(a.means2d) + rec * C;
-      for (int l = 0; l < C; ++l) s_mean[l * NB + threadIdx.x] = mp[l];
+      for (int l = 0; l < C; ++l) {
+        const float2 mu = mp[l];
+        s_mean[l * NB + threadIdx.x] = mu;
+        const bool hit = (mu.x + hx >= bx0) && (mu.x - hx <= bx1) && (mu.y + hy >= by0) &&
+                         (mu.y - hy <= by1);
+        mask |= (uint32_t)hit << l;
+      }
       s_gid[threadIdx.x] = gid;
     }
+    s_vm[threadIdx.x] = mask;
+    if (!compact) {
+      __syncthreads();
+      return;
+    }
+    for (int l = 0; l < C; ++l) {
+      const unsigned b = __ballot_sync(0xffffffffu, (mask >> l) & 1u);
+      if (lane == 0) s_cnt[l * (NW + 1) + warp] = __popc(b);
+    }
+    __syncthreads();
+    if (threadIdx.x < C) {
+      int run = 0;
+      for (int w = 0; w < NW; ++w) {
+        const int c = s_cnt[threadIdx.x * (NW + 1) + w];
+        s_cnt[threadIdx.x * (NW + 1) + w] = run;
+        run += c;
+      }
+      s_cnt[threadIdx.x * (NW + 1) + NW] = run;
+    }
+    __syncthreads();
+    for (int l = 0; l < C; ++l) {
+      const unsigned b = __ballot_sync(0xffffffffu, (mask >> l) & 1u);
+      if ((mask >> l) & 1u)
+        s_idx[l * NB + s_cnt[l * (NW + 1) + warp] + __popc(b & lt)] = (uint16_t)threadIdx.x;
+    }
+    __syncthreads();
   };
-  // the opacity of an entry for this subpixel, exactly as the forward blend
-  // computes it (0 when skipped); also returns e^power and whether clamped
-  auto opacity_of = [&](int gi, float& vexp, bool& clamped) -> float {
-    const float4 co = s_co[gi];
-    const float2 mu = s_mean[slot * NB + gi];
-    const float dx = px - mu.x, dy = py - mu.y;
-    // the forward blend's pre-scaled conic and order of operations
-    const float power = quad_power(-0.5f * kLog2e * co.x, -kLog2e * co.y, -0.5f * kLog2e * co.z, dx, dy);
-    if (power > 0.f) return 0.f;
-    const float v = co.w * ex2_approx(power);
-    if (!(v >= kAlphaMin)) return 0.f;
-    vexp = v / co.w;
-    clamped = v > kAlphaMax;
-    return fminf(kAlphaMax, v);
+  // add the staged entry's shared-memory gradient sums to global memory
+  // (entry base + threadIdx.x, by the thread that staged it) and clear them
+  auto flush = [&](uint32_t base, uint32_t end) {
+    const uint32_t e = base + threadIdx.x;
+    if (e < end && s_vm[threadIdx.x]) {
+      const uint32_t gid = s_gid[threadIdx.x];
+      const size_t rec = (size_t)k * a.M + gid;
+      const float4 d = s_gco[threadIdx.x];
+      if (d.x != 0.f) atomicAdd(&gr.grad_conic[4 * rec + 0], d.x);
+      if (d.y != 0.f) atomicAdd(&gr.grad_conic[4 * rec + 1], d.y);
+      if (d.z != 0.f) atomicAdd(&gr.grad_conic[4 * rec + 2], d.z);
+      if (d.w != 0.f) atomicAdd(&gr.grad_opac[gid], d.w);
+      const float4 dc = s_gcol[threadIdx.x];
+      if (dc.x != 0.f) atomicAdd(&gr.grad_color[4 * rec + 0], dc.x);
+      if (dc.y != 0.f) atomicAdd(&gr.grad_color[4 * rec + 1], dc.y);
+      if (dc.z != 0.f) atomicAdd(&gr.grad_color[4 * rec + 2], dc.z);
+      float* gmg = gr.grad_means2d + 2 * rec * C;
+      for (int l = 0; l < C; ++l) {
+        const float2 dm = s_gmean[l * NB + threadIdx.x];
+        if (dm.x != 0.f) atomicAdd(gmg + 2 * l, dm.x);
+        if (dm.y != 0.f) atomicAdd(gmg + 2 * l + 1, dm.y);
+      }
+    }
+    s_gco[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+    s_gcol[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int l = 0; l < C; ++l) s_gmean[l * NB + threadIdx.x] = make_float2(0.f, 0.f);
   };
 
-  // forward replay: final transmittance and the first entry not added
-  float T = 1.f;
-  uint32_t stop = rg.y;  // global list index where this subpixel stopped
-  for (uint32_t base = rg.x; base < rg.y; base += (uint32_t)NB) {
-    if (!__syncthreads_or(act)) break;
-    stage(base);
-    __syncthreads();
-    if (!act) continue;
-    const int nbatch = (int)min((uint32_t)NB, rg.y - base);
-    for (int gi = 0; gi < nbatch; ++gi) {
-      float ve;
-      bool cl;
-      const float alpha = opacity_of(gi, ve, cl);
-      if (alpha == 0.f) continue;
-      const float Tn = T * (1.f - alpha);
-      if (Tn < kTMin) {
-        act = false;
-        stop = base + (uint32_t)gi;
-        break;
-      }
-      T = Tn;
+  // runs longer than the block are processed in chunks of blockDim subpixels
+  for (int chunk = 0; chunk < n; chunk += NB) {
+    const int r = chunk + threadIdx.x;
+    const bool live = r < n;
+    float px = 0.f, py = 0.f, G = 0.f;
+    int slot = 0, ch = 0;
+    if (live) {
+      const uint32_t e = a.psi[(size_t)t * g.cap + s0 + r];
+      const int view = (int)(e >> 16);
+      const int loc = (int)(e & 0xffffu);
+      const int xl = (loc / 3) % g.TW, yl = (loc / 3) / g.TW;
+      const int x = tx * g.TW + xl, y = ty * g.TH + yl;
+      ch = loc % 3;
+      px = (float)x + 0.5f;
+      py = (float)y + 0.5f;
+      slot = view - k * C;
+      G = gr.grad_out[((int64_t)y * g.W + x) * 3 + ch];
     }
-  }
-  // back to front over [rg.x, stop): R is the colour of everything behind
-  const float bgc = ch == 0 ? a.bg[0] : (ch == 1 ? a.bg[1] : a.bg[2]);
-  float R = bgc;
-  uint32_t last = live ? stop : rg.x;
-  // the block's furthest stop
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = rg.x;
-  __syncthreads();
-  if (live) atomicMax(&s_last, last);
-  __syncthreads();
-  const uint32_t end = s_last;
-  if (end == rg.x) continue;
-  const uint32_t nb_total = (end - rg.x + NB - 1) / NB;
-  for (int b = (int)nb_total - 1; b >= 0; --b) {
-    const uint32_t base = rg.x + (uint32_t)b * NB;
+    // the opacity of an entry for this subpixel, exactly as the forward
+    // blend computes it (0 when skipped); also e^power and whether clamped
+    auto opacity_of = [&](int gi, float& vexp, bool& clamped) -> float {
+      const float4 co = s_co[gi];
+      const float2 mu = s_mean[slot * NB + gi];
+      const float dx = px - mu.x, dy = py - mu.y;
+      // the forward blend's pre-scaled conic and order of operations
+      const float power = quad_power(-0.5f * kLog2e * co.x, -kLog2e * co.y, -0.5f * kLog2e * co.z, dx, dy);
+      if (power > 0.f) return 0.f;
+      const float v = co.w * ex2_approx(power);
+      if (!(v >= kAlphaMin)) return 0.f;
+      vexp = v / co.w;
+      clamped = v > kAlphaMax;
+      return fminf(kAlphaMax, v);
+    };
+
+    // final transmittance and the list index of the first entry not added
+    float T = 1.f;
+    uint32_t last = rg.x;
+    if (KEPT) {
+      if (live) {
+        const uint2 kp = a.keep[(size_t)t * g.cap + s0 + r];
+        last = kp.x;
+        T = __uint_as_float(kp.y);
+      }
+    } else {
+      bool act = live;
+      uint32_t stop = rg.y;
+      for (uint32_t base = rg.x; base < rg.y; base += (uint32_t)NB) {
+        if (!__syncthreads_or(act)) break;
+        stage(base, true);
+        if (!act) continue;
+        const uint16_t* idx = s_idx + slot * NB;
+        const int cnt = s_cnt[slot * (NW + 1) + NW];
+        for (int q = 0; q < cnt; ++q) {
+          const int gi = idx[q];
+          float ve;
+          bool cl;
+          const float alpha = opacity_of(gi, ve, cl);
+          if (alpha == 0.f) continue;
+          const float Tn = T * (1.f - alpha);
+          if (Tn < kTMin) {
+            act = false;
+            stop = base + (uint32_t)gi;
+            break;
+          }
+          T = Tn;
+        }
+      }
+      if (live) last = stop;
+    }
+    // the block's furthest stop
     __syncthreads();
-    stage(base);
+    if (threadIdx.x == 0) s_last = rg.x;
     __syncthreads();
-    const int nbatch = (int)min((uint32_t)NB, end - base);
-    for (int gi = nbatch - 1; gi >= 0; --gi) {
-      float d_mx = 0.f, d_my = 0.f, d_a = 0.f, d_b = 0.f, d_c = 0.f, d_o = 0.f, d_col = 0.f;
-      bool any = false;
-      if (live && base + (uint32_t)gi < last) {
-        float ve = 0.f;
-        bool cl = false;
-        const float alpha = opacity_of(gi, ve, cl);
-        if (alpha > 0.f) {
-          any = true;
-          const float4 col4 = s_col[gi];
-          const float c = ch == 0 ? col4.x : (ch == 1 ? col4.y : col4.z);
-          const float Ti = T / (1.f - alpha);  // transmittance in front of this entry
-          d_col = alpha * Ti * G;
-          const float dalpha = (c - R) * Ti * G;
-          R = c * alpha + (1.f - alpha) * R;
-          T = Ti;
-          if (!cl) {
-            const float4 co = s_co[gi];
-            const float2 mu = s_mean[slot * NB + gi];
-            const float dx = px - mu.x, dy = py - mu.y;
-            const float dpower = dalpha * alpha;  // d alpha / d power = alpha
-            d_o = dalpha * ve;
-            // power = -(a dx^2 + 2 b dx dy + c dy^2) / 2, dx = px - mu_x
-            d_mx = dpower * (co.x * dx + co.y * dy);
-            d_my = dpower * (co.y * dx + co.z * dy);
-            d_a = -0.5f * dpower * dx * dx;
-            d_b = -dpower * dx * dy;
-            d_c = -0.5f * dpower * dy * dy;
+    if (live) atomicMax(&s_last, last);
+    __syncthreads();
+    const uint32_t end = s_last;
+    if (end == rg.x) continue;
+
+    // back to front over [rg.x, last): R is the colour of everything behind.
+    // The mean gradients are per view: the warp sums them for its lowest
+    // view v0 and highest view v1 (a view strictly between them adds its
+    // own directly).
+    float R = ch == 0 ? a.bg[0] : (ch == 1 ? a.bg[1] : a.bg[2]);
+    const unsigned wm = __reduce_or_sync(0xffffffffu, live ? (1u << slot) : 0u);
+    const int v0 = wm ? __ffs(wm) - 1 : 0;
+    const int v1 = wm ? 31 - __clz(wm) : 0;
+    const uint32_t nb_total = (end - rg.x + NB - 1) / NB;
+    s_gco[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+    s_gcol[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int l = 0; l < C; ++l) s_gmean[l * NB + threadIdx.x] = make_float2(0.f, 0.f);
+    for (int b = (int)nb_total - 1; b >= 0; --b) {
+      const uint32_t base = rg.x + (uint32_t)b * NB;
+      // the thread that staged entry i of the batch behind flushes it before
+      // staging entry i of this one: no barrier between the two
+      if (b != (int)nb_total - 1) flush(base + (uint32_t)NB, end);
+      stage(base, false);
+      for (int w32 = NW - 1; wm != 0u && w32 >= 0; --w32) {
+        unsigned h = __ballot_sync(0xffffffffu, (s_vm[w32 * 32 + lane] & wm) != 0u);
+        while (h) {
+          const int j = 31 - __clz(h);
+          h &= ~(1u << j);
+          const int gi = w32 * 32 + j;
+          float v[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[i] = 0.f;
+          bool any = false;
+          if (live && base + (uint32_t)gi < last && ((s_vm[gi] >> slot) & 1u)) {
+            float ve = 0.f;
+            bool cl = false;
+            const float alpha = opacity_of(gi, ve, cl);
+            if (alpha != 0.f) {
+              any = true;
+              const float4 col4 = s_col[gi];
+              const float c = ch == 0 ? col4.x : (ch == 1 ? col4.y : col4.z);
+              const float Ti = T / (1.f - alpha);  // transmittance in front of this entry
+              const float dcol = alpha * Ti * G;
+              v[4] = ch == 0 ? dcol : 0.f;
+              v[5] = ch == 1 ? dcol : 0.f;
+              v[6] = ch == 2 ? dcol : 0.f;
+              const float dalpha = (c - R) * Ti * G;
+              R = c * alpha + (1.f - alpha) * R;
+              T = Ti;
+              if (!cl) {
+                const float4 co = s_co[gi];
+                const float2 mu = s_mean[slot * NB + gi];
+                const float dx = px - mu.x, dy = py - mu.y;
+                const float dpower = dalpha * alpha;  // d alpha / d power = alpha
+                // power = -(a dx^2 + 2 b dx dy + c dy^2) / 2, dx = px - mu_x
+                v[0] = -0.5f * dpower * dx * dx;
+                v[1] = -dpower * dx * dy;
+                v[2] = -0.5f * dpower * dy * dy;
+                v[3] = dalpha * ve;
+                const float dmx = dpower * (co.x * dx + co.y * dy);
+                const float dmy = dpower * (co.y * dx + co.z * dy);
+                if (slot == v0) {
+                  v[7] = dmx;
+                  v[8] = dmy;
+                } else if (slot == v1) {
+                  v[9] = dmx;
+                  v[10] = dmy;
+                } else {
+                  float* gm = reinterpret_cast<float*>(&s_gmean[slot * NB + gi]);
+                  atomicAdd(gm + 0, dmx);
+                  atomicAdd(gm + 1, dmy);
+                }
+              }
+            }
+          }
+          if (!__any_sync(0xffffffffu, any)) continue;
+          // lanes 2i and 2i + 1 end with the warp's sum of v[i]
+          const float sum = warp_transpose_sum16(v, lane);
+          const int i = lane >> 1;
+          if ((lane & 1) == 0 && i < 11 && sum != 0.f) {
+            float* dst;
+            if (i < 4)
+              dst = reinterpret_cast<float*>(&s_gco[gi]) + i;
+            else if (i < 7)
+              dst = reinterpret_cast<float*>(&s_gcol[gi]) + (i - 4);
+            else
+              dst = reinterpret_cast<float*>(&s_gmean[(i < 9 ? v0 : v1) * NB + gi]) + ((i - 7) & 1);
+            atomicAdd(dst, sum);
           }
         }
       }
-      // conic and opacity are shared by the warp's lanes: reduce first
-      const unsigned want = __ballot_sync(0xffffffffu, any);
-      if (!want) continue;
-      float ra = d_a, rb = d_b, rc = d_c, ro = d_o;
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        ra += __shfl_xor_sync(0xffffffffu, ra, off);
-        rb += __shfl_xor_sync(0xffffffffu, rb, off);
-        rc += __shfl_xor_sync(0xffffffffu, rc, off);
-        ro += __shfl_xor_sync(0xffffffffu, ro, off);
-      }
-      const uint32_t gid = s_gid[gi];
-      const size_t rec = (size_t)k * a.M + gid;
-      if (lane == __ffs(want) - 1) {
-        atomicAdd(&gr.grad_conic[4 * rec + 0], ra);
-        atomicAdd(&gr.grad_conic[4 * rec + 1], rb);
-        atomicAdd(&gr.grad_conic[4 * rec + 2], rc);
-        atomicAdd(&gr.grad_opac[gid], ro);
-      }
-      if (any) {
-        atomicAdd(&gr.grad_color[4 * rec + ch], d_col);
-        float* gm = gr.grad_means2d + 2 * (rec * C + slot);
-        atomicAdd(gm, d_mx);
-        atomicAdd(gm + 1, d_my);
-      }
+      __syncthreads();
     }
+    flush(rg.x, end);
   }
-  }  // chunk
 }
 
 // ---------------------------------------------------------------------------
@@ -412,10 +555,20 @@ cudaError_t launch_blend_backward(const PanelGeom& g, const BlendArgs& a, const 
   if ((int64_t)g.K * g.T == 0) return cudaSuccess;
   const int need = a.max_segment > 0 ? a.max_segment : 1;
   const int block = min(256, ((need + 31) / 32) * 32);
-  const size_t smem = (size_t)block * (2 * sizeof(float4) + g.C * sizeof(float2) + sizeof(uint32_t));
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_blend_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_blend_backward<<<(unsigned)((int64_t)g.K * g.T), block, smem, s>>>(g, a, gr);
+  const int nw = block / 32;
+  const size_t smem = (size_t)block * (4 * sizeof(float4) + 2 * g.C * sizeof(float2) + 2 * sizeof(uint32_t)) +
+                      (((size_t)g.C * block + 1) & ~(size_t)1) * sizeof(uint16_t) +
+                      (size_t)g.C * (nw + 1) * sizeof(int);
+  const unsigned grid = (unsigned)((int64_t)g.K * g.T);
+  if (a.keep) {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_blend_backward<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_blend_backward<true><<<grid, block, smem, s>>>(g, a, gr);
+  } else {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_blend_backward<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_blend_backward<false><<<grid, block, smem, s>>>(g, a, gr);
+  }
   note_launches(1);
   return cudaGetLastError();
 }

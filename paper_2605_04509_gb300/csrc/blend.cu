@@ -63,6 +63,7 @@ __device__ __forceinline__ void blend_run(const PanelGeom& g, const BlendArgs& a
   const float by1 = (float)min(ty * g.TH + g.TH, g.H) - 0.5f + 1.f;
 
   float px[R], py[R], T[R], acc[R];
+  uint32_t stop_at[R];  // list index where the walk stopped
   int slot[R], ch[R];
   int64_t oidx[R];
   bool act[R];
@@ -73,6 +74,7 @@ __device__ __forceinline__ void blend_run(const PanelGeom& g, const BlendArgs& a
     act[m] = r < n;
     T[m] = 1.f;
     acc[m] = 0.f;
+    stop_at[m] = rg.y;
     px[m] = py[m] = 0.f;
     slot[m] = 0;
     ch[m] = 0;
@@ -213,6 +215,7 @@ __device__ __forceinline__ void blend_run(const PanelGeom& g, const BlendArgs& a
           if (apply(gi, oc.x * ex2_approx(power), oc.y)) stop_q = q;
         }
       }
+      if (stop >= 0) stop_at[m] = base + (uint32_t)stop;
       if (COUNT) n_eval += stop_q >= 0 ? (unsigned long long)(stop_q + 1) : (unsigned long long)cnt;
       // list entries walked in this batch, skipped ones included
       if (COUNT) n_visit += stop >= 0 ? (unsigned long long)(stop + 1) : (unsigned long long)nbatch;
@@ -223,6 +226,8 @@ __device__ __forceinline__ void blend_run(const PanelGeom& g, const BlendArgs& a
     if (!live[m]) continue;
     const float bg = ch[m] == 0 ? a.bg[0] : (ch[m] == 1 ? a.bg[1] : a.bg[2]);
     a.out[oidx[m]] = acc[m] + T[m] * bg;
+    if (a.keep)
+      a.keep[(size_t)t * g.cap + s0 + threadIdx.x + m * NB] = make_uint2(stop_at[m], __float_as_uint(T[m]));
   }
   if (COUNT) {
     unsigned long long cv = n_visit, ce = n_eval;

@@ -104,11 +104,13 @@ struct lfd_plan {
   DevBuf host_in[5];  // device copies of host Gaussians (lfd_render_host)
   DevBuf image;       // device image for lfd_render_host
   DevBuf g_means2d, g_conic, g_color, g_opac;  // backward scratch
+  DevBuf keep;  // LFD_FLAG_KEEP_BLEND_STATE: [T][cap] stop index, final T
   unsigned long long* h_small = nullptr;  // pinned
   // last frame
   int64_t last_P = -1;
   int64_t last_M = -1;
   bool last_from_render = false;
+  bool last_kept = false;  // the last frame wrote the blend state into keep
   int last_key_buf = 0;
   int last_val_buf = 0;
   int last_sort_mode = 0;
@@ -232,7 +234,7 @@ void lfd_plan_destroy(lfd_plan* p) {
                     &p->pair_key[1], &p->pair_val[0], &p->pair_val[1], &p->radix_tmp,
                     &p->ranges,     &p->small,     &p->host_in[0],  &p->host_in[1],
                     &p->host_in[2], &p->host_in[3], &p->host_in[4], &p->image,
-                    &p->g_means2d,  &p->g_conic,   &p->g_color,     &p->g_opac};
+                    &p->g_means2d,  &p->g_conic,   &p->g_color,     &p->g_opac, &p->keep};
   for (DevBuf* b : bufs) b->release();
   if (p->h_small) cudaFreeHost(p->h_small);
   for (auto& set : p->ev)
@@ -350,7 +352,13 @@ int lfd_plan_get_info(const lfd_plan* p, lfd_plan_info* out) {
 
 int lfd_set_flags(lfd_plan* p, int32_t flags) {
   if (!p) return fail(LFD_ERR_INVALID, "NULL plan");
-  if (flags & ~(LFD_FLAG_STAGE_TIMING | LFD_FLAG_COUNT_EVALS)) return fail(LFD_ERR_INVALID, "unknown flag");
+  if (flags & ~(LFD_FLAG_STAGE_TIMING | LFD_FLAG_COUNT_EVALS | LFD_FLAG_KEEP_BLEND_STATE))
+    return fail(LFD_ERR_INVALID, "unknown flag");
+  if (flags & LFD_FLAG_KEEP_BLEND_STATE) {
+    // allocated here so that frames in capacity mode stay allocation-free
+    const int rc = p->keep.ensure((size_t)p->g.T * p->g.cap * sizeof(uint2));
+    if (rc != LFD_OK) return rc;
+  }
   p->flags = flags;
   return LFD_OK;
 }
@@ -574,6 +582,8 @@ static int render_projected_impl(lfd_plan* p, int64_t M, const float* means2d,
   ba.P_dev = d_small;
   ba.P_cap = P;
   ba.subpixels_per_thread = p->opts.subpixels_per_thread;
+  const bool kept = (p->flags & LFD_FLAG_KEEP_BLEND_STATE) && p->opts.remap && !p->fullframe;
+  ba.keep = kept ? p->keep.as<uint2>() : nullptr;
   if (p->fullframe)
     LFD_CUDA(launch_blend_fullframe(g, ba, s));
   else if (p->opts.remap)
@@ -590,6 +600,7 @@ static int render_projected_impl(lfd_plan* p, int64_t M, const float* means2d,
   p->last_P = capmode ? -2 : (int64_t)P;  // -2: the count is on the device
   p->last_M = M;
   p->last_from_render = projected_here;
+  p->last_kept = kept;
   p->last_key_buf = kb;
   p->last_val_buf = kb;
   p->last_sort_mode = p->opts.sort_mode;
@@ -702,6 +713,7 @@ int lfd_render_backward(lfd_plan* p, const lfd_gaussians* gs, const lfd_camera* 
   ba.eval_counter = nullptr;
   ba.max_segment = p->max_segment;
   ba.V = p->V;
+  ba.keep = p->last_kept ? p->keep.as<uint2>() : nullptr;
   BlendGrads gr;
   gr.grad_out = grad_rgb;
   gr.grad_means2d = p->g_means2d.as<float>();

@@ -225,6 +225,10 @@ struct BlendArgs {
   const unsigned long long* P_dev = nullptr;
   unsigned long long P_cap = 0;
   int subpixels_per_thread = 0;  // 0: automatic
+  // non-null: per Psi position [T][cap], the list index where the subpixel's
+  // walk stopped (the range end if it never saturated) and the bits of its
+  // final transmittance; written by the remapped blend, read by the backward
+  uint2* keep = nullptr;
 };
 cudaError_t launch_blend(const PanelGeom& g, const BlendArgs& a, cudaStream_t s);
 

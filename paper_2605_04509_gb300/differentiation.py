@@ -6,8 +6,9 @@ perturbed by N(0, 0.01) (seed 6).
 
     python -m paper_2605_04509_gb300.differentiation [--steps 10]
 
-Each step is forward (lfd_render) + loss + backward (lfd_render_backward:
-the blend replayed per (tile, cluster) run back to front, then the 3DGS
+Each step is forward (lfd_render, keeping each subpixel's final
+transmittance and stop position) + loss + backward (lfd_render_backward: each
+(tile, cluster) run walked back to front from the kept state, then the 3DGS
 projection chain) through lfd.render_autograd, then one plain gradient step
 on the means. Prints steps/s, the forward and backward times, the loss
 before and after, and the gradient norms per parameter group. The gradients

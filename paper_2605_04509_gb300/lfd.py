@@ -26,6 +26,7 @@ SORT_DEPTH_FIRST = 0
 SORT_KEY64 = 1
 FLAG_STAGE_TIMING = 1
 FLAG_COUNT_EVALS = 2
+FLAG_KEEP_BLEND_STATE = 4
 
 
 class LFDError(RuntimeError):
@@ -211,6 +212,7 @@ class Plan:
         h = _P()
         _check(L.lfd_plan_create(ct.byref(cp), ct.byref(co), ct.byref(h)))
         self._h = h
+        self.flags = 0
         self.tile = tuple(tile)
         self.views_per_cluster = views_per_cluster
         self.sort_mode = sort_mode
@@ -233,6 +235,7 @@ class Plan:
 
     def set_flags(self, flags: int):
         _check(load().lfd_set_flags(self._h, flags))
+        self.flags = flags
 
     def tables(self):
         p = self.panel
@@ -388,8 +391,13 @@ def scene_to_device(scene: Dict[str, np.ndarray], device="cuda", attr_dtype=None
 
 def render_autograd(plan: "Plan", cams: np.ndarray, means, scales, quats, opacities, sh):
     """Differentiable interlaced render: forward through lfd_render, backward
-    through lfd_render_backward (a torch.autograd.Function)."""
+    through lfd_render_backward (a torch.autograd.Function). Turns on the
+    plan's FLAG_KEEP_BLEND_STATE so that the backward starts from the
+    forward's per-subpixel state."""
     import torch
+
+    if not plan.flags & FLAG_KEEP_BLEND_STATE:
+        plan.set_flags(plan.flags | FLAG_KEEP_BLEND_STATE)
 
     class _Render(torch.autograd.Function):
         @staticmethod

@@ -4,6 +4,10 @@
 Setting of the differentiation workload, reduced to its check subset: 200
 Gaussians, a 64x64 panel with 24 views (slant 0.2 rad, pitch 4.8), an L2 loss
 to a target rendered from a copy whose means are perturbed by N(0, 0.01).
+Both backward forms are covered: from the blend state kept by the forward
+frame, and re-blending the lists. Clusters of 24 views give runs longer than
+a block (processed in chunks); the 45-view panel (pitch 4.6) puts two or
+three views in one warp.
 """
 import math
 
@@ -25,9 +29,9 @@ from paper_2605_04509_gb300 import lfd  # noqa: E402
 KEYS = ("means", "scales", "quats", "opacities", "sh")
 
 
-def case(c):
-    panel = synth.Panel(64, 64, 24, math.tan(0.2), 4.8, 0.0)
-    rig = synth.Rig(24, 40.0, 4.0, 50.0)
+def case(c, views=24, pitch=4.8):
+    panel = synth.Panel(64, 64, views, math.tan(0.2), pitch, 0.0)
+    rig = synth.Rig(views, 40.0, 4.0, 50.0)
     scene = synth.uniform_scene(200, 5, half_extent=0.6)
     cams = synth.arc_cameras(rig, panel.width, panel.height)
     V = oracle.view_index(panel)
@@ -39,10 +43,11 @@ def case(c):
     return panel, scene, cams, V, target
 
 
-@pytest.mark.parametrize("c", [1, 8])
-def test_gradients_match_fp64_autograd(c):
-    panel, scene, cams, V, target = case(c)
+def check_against_oracle(c, kept, views=24, pitch=4.8):
+    panel, scene, cams, V, target = case(c, views, pitch)
     plan = lfd.Plan(panel, views_per_cluster=c)
+    if kept:
+        plan.set_flags(lfd.FLAG_KEEP_BLEND_STATE)
     s = lfd.scene_to_device(scene)
     img, _ = plan.render(s, cams)
     tgt = torch.from_numpy(target.astype(np.float32)).cuda()
@@ -60,6 +65,38 @@ def test_gradients_match_fp64_autograd(c):
     plan.close()
 
 
+@pytest.mark.parametrize("kept", [False, True])
+@pytest.mark.parametrize("c", [1, 8, 24])
+def test_gradients_match_fp64_autograd(c, kept):
+    check_against_oracle(c, kept)
+
+
+@pytest.mark.parametrize("kept", [False, True])
+def test_gradients_match_fp64_autograd_several_views_per_warp(kept):
+    check_against_oracle(8, kept, views=45, pitch=4.6)
+
+
+def test_kept_state_matches_replay():
+    panel, scene, cams, V, target = case(8)
+    s = lfd.scene_to_device(scene)
+    tgt = torch.from_numpy(target.astype(np.float32)).cuda()
+    out = []
+    for kept in (False, True):
+        plan = lfd.Plan(panel, views_per_cluster=8)
+        if kept:
+            plan.set_flags(lfd.FLAG_KEEP_BLEND_STATE)
+        img, _ = plan.render(s, cams)
+        out.append((img.clone(), plan.backward(s, cams, 2.0 * (img - tgt))))
+        plan.close()
+    # the kept state leaves the image bit-identical; the gradients differ
+    # only by the order of the floating-point atomics that sum them
+    assert torch.equal(out[0][0], out[1][0])
+    for key in KEYS:
+        err = float((out[0][1][key] - out[1][1][key]).abs().max())
+        scale = float(out[0][1][key].abs().max())
+        assert err <= 1e-4 * scale, (key, err, scale)
+
+
 def test_autograd_function_matches_entry_point():
     panel, scene, cams, V, target = case(8)
     plan = lfd.Plan(panel, views_per_cluster=8)
@@ -70,6 +107,10 @@ def test_autograd_function_matches_entry_point():
     ((img - tgt) ** 2).sum().backward()
     img2, _ = plan.render(s, cams)
     direct = plan.backward(s, cams, 2.0 * (img2 - tgt))
+    # the gradients are summed with floating-point atomics, whose order varies
+    # from run to run: compare against the gradient's own scale
     for key in KEYS:
-        assert torch.allclose(leaves[key].grad, direct[key], rtol=1e-5, atol=1e-7), key
+        err = float((leaves[key].grad - direct[key]).abs().max())
+        scale = float(direct[key].abs().max())
+        assert err <= 1e-4 * scale, (key, err, scale)
     plan.close()
