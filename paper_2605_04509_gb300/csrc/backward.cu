@@ -16,13 +16,16 @@ constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTMin = 1e-4f;
 
-// Sum 16 values over a warp in 16 shuffles: each butterfly stage trades half
-// of the values still held with the partner lane, so lane l ends with the
-// full sum of v[l >> 1] (v is overwritten). All 32 lanes must call it.
-__device__ __forceinline__ float warp_transpose_sum16(float (&v)[16], int lane) {
+// Sum NV values (a power of two up to 32) over a warp with NV - 1 + 5 -
+// log2(NV) shuffles: each butterfly stage trades half of the values still
+// held with the partner lane, so lane l ends with the full sum of
+// v[l >> (5 - log2(NV))] (v is overwritten). All 32 lanes must call it.
+template <int NV>
+__device__ __forceinline__ float warp_transpose_sum(float (&v)[NV], int lane) {
   const unsigned full = 0xffffffffu;
+  int off = 16;
 #pragma unroll
-  for (int half = 8, off = 16; half >= 1; half >>= 1, off >>= 1) {
+  for (int half = NV / 2; half >= 1; half >>= 1, off >>= 1) {
     const bool up = (lane & off) != 0;
 #pragma unroll
     for (int i = 0; i < half; ++i) {
@@ -31,7 +34,10 @@ __device__ __forceinline__ float warp_transpose_sum16(float (&v)[16], int lane) 
       v[i] = keep + __shfl_xor_sync(full, send, off);
     }
   }
-  return v[0] + __shfl_xor_sync(full, v[0], 1);
+  float r = v[0];
+#pragma unroll
+  for (; off >= 1; off >>= 1) r += __shfl_xor_sync(full, r, off);
+  return r;
 }
 
 // ---------------------------------------------------------------------------
@@ -47,8 +53,9 @@ __device__ __forceinline__ float warp_transpose_sum16(float (&v)[16], int lane) 
 // others have alpha < 1/255 there). Psi lists a run's subpixels view by
 // view, so a warp holds one or two views: it walks the entries seen by any
 // of them, all lanes on the same entry, and sums each entry's gradients over
-// the warp (16-value transpose reduction) into shared memory; a batch's sums
-// go to global memory once per entry, by the thread that staged the entry.
+// the warp (16-value transpose reduction). Conic, opacity and colour sums
+// collect in shared memory and go to global memory once per entry and batch,
+// by the thread that staged the entry; mean sums go to global memory at once.
 // ---------------------------------------------------------------------------
 template <bool KEPT>
 __global__ void __launch_bounds__(256) k_blend_backward(PanelGeom g, BlendArgs a, BlendGrads gr) {
@@ -61,9 +68,9 @@ __global__ void __launch_bounds__(256) k_blend_backward(PanelGeom g, BlendArgs a
   float4* s_gco = smem + 2 * NB;                                // d(a, b, c), d opacity
   float4* s_gcol = smem + 3 * NB;                               // d colour
   float2* s_mean = reinterpret_cast<float2*>(smem + 4 * NB);    // [C][NB]
-  float2* s_gmean = s_mean + C * NB;                            // [C][NB]
-  uint32_t* s_gid = reinterpret_cast<uint32_t*>(s_gmean + C * NB);
+  uint32_t* s_gid = reinterpret_cast<uint32_t*>(s_mean + C * NB);
   uint32_t* s_vm = s_gid + NB;                                  // view bits of each entry
+  // per-view lists of the re-blend (without KEPT only)
   uint16_t* s_idx = reinterpret_cast<uint16_t*>(s_vm + NB);     // [C][NB]
   int* s_cnt = reinterpret_cast<int*>(s_idx + ((C * NB + 1) & ~1));  // [C][NW + 1]
   __shared__ uint32_t s_last;
@@ -135,8 +142,9 @@ __global__ void __launch_bounds__(256) k_blend_backward(PanelGeom g, BlendArgs a
     }
     __syncthreads();
   };
-  // add the staged entry's shared-memory gradient sums to global memory
-  // (entry base + threadIdx.x, by the thread that staged it) and clear them
+  // add the staged entry's shared-memory sums (conic, opacity and colour
+  // gradients) to global memory (entry base + threadIdx.x, by the thread
+  // that staged it) and clear them
   auto flush = [&](uint32_t base, uint32_t end) {
     const uint32_t e = base + threadIdx.x;
     if (e < end && s_vm[threadIdx.x]) {
@@ -151,16 +159,9 @@ __global__ void __launch_bounds__(256) k_blend_backward(PanelGeom g, BlendArgs a
       if (dc.x != 0.f) atomicAdd(&gr.grad_color[4 * rec + 0], dc.x);
       if (dc.y != 0.f) atomicAdd(&gr.grad_color[4 * rec + 1], dc.y);
       if (dc.z != 0.f) atomicAdd(&gr.grad_color[4 * rec + 2], dc.z);
-      float* gmg = gr.grad_means2d + 2 * rec * C;
-      for (int l = 0; l < C; ++l) {
-        const float2 dm = s_gmean[l * NB + threadIdx.x];
-        if (dm.x != 0.f) atomicAdd(gmg + 2 * l, dm.x);
-        if (dm.y != 0.f) atomicAdd(gmg + 2 * l + 1, dm.y);
-      }
     }
     s_gco[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
     s_gcol[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int l = 0; l < C; ++l) s_gmean[l * NB + threadIdx.x] = make_float2(0.f, 0.f);
   };
 
   // runs longer than the block are processed in chunks of blockDim subpixels
@@ -190,9 +191,10 @@ __global__ void __launch_bounds__(256) k_blend_backward(PanelGeom g, BlendArgs a
       // the forward blend's pre-scaled conic and order of operations
       const float power = quad_power(-0.5f * kLog2e * co.x, -kLog2e * co.y, -0.5f * kLog2e * co.z, dx, dy);
       if (power > 0.f) return 0.f;
-      const float v = co.w * ex2_approx(power);
+      const float ev = ex2_approx(power);
+      const float v = co.w * ev;
       if (!(v >= kAlphaMin)) return 0.f;
-      vexp = v / co.w;
+      vexp = ev;
       clamped = v > kAlphaMax;
       return fminf(kAlphaMax, v);
     };
@@ -242,17 +244,19 @@ __global__ void __launch_bounds__(256) k_blend_backward(PanelGeom g, BlendArgs a
     if (end == rg.x) continue;
 
     // back to front over [rg.x, last): R is the colour of everything behind.
-    // The mean gradients are per view: the warp sums them for its lowest
-    // view v0 and highest view v1 (a view strictly between them adds its
-    // own directly).
+    // Per entry, the warp sums its conic, opacity and colour gradients and
+    // the mean gradients of its lowest view v0 and highest view v1 (16
+    // slots, 12 used); the reducing lanes add the mean sums to global memory
+    // directly (a view strictly between v0 and v1 adds its own).
     float R = ch == 0 ? a.bg[0] : (ch == 1 ? a.bg[1] : a.bg[2]);
     const unsigned wm = __reduce_or_sync(0xffffffffu, live ? (1u << slot) : 0u);
     const int v0 = wm ? __ffs(wm) - 1 : 0;
     const int v1 = wm ? 31 - __clz(wm) : 0;
+    // the warp walks no entry at or past its furthest stop
+    const uint32_t wlast = __reduce_max_sync(0xffffffffu, live ? last : rg.x);
     const uint32_t nb_total = (end - rg.x + NB - 1) / NB;
     s_gco[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
     s_gcol[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int l = 0; l < C; ++l) s_gmean[l * NB + threadIdx.x] = make_float2(0.f, 0.f);
     for (int b = (int)nb_total - 1; b >= 0; --b) {
       const uint32_t base = rg.x + (uint32_t)b * NB;
       // the thread that staged entry i of the batch behind flushes it before
@@ -260,7 +264,8 @@ __global__ void __launch_bounds__(256) k_blend_backward(PanelGeom g, BlendArgs a
       if (b != (int)nb_total - 1) flush(base + (uint32_t)NB, end);
       stage(base, false);
       for (int w32 = NW - 1; wm != 0u && w32 >= 0; --w32) {
-        unsigned h = __ballot_sync(0xffffffffu, (s_vm[w32 * 32 + lane] & wm) != 0u);
+        const uint32_t e_lane = base + (uint32_t)(w32 * 32 + lane);
+        unsigned h = __ballot_sync(0xffffffffu, e_lane < wlast && (s_vm[w32 * 32 + lane] & wm) != 0u);
         while (h) {
           const int j = 31 - __clz(h);
           h &= ~(1u << j);
@@ -277,7 +282,7 @@ __global__ void __launch_bounds__(256) k_blend_backward(PanelGeom g, BlendArgs a
               any = true;
               const float4 col4 = s_col[gi];
               const float c = ch == 0 ? col4.x : (ch == 1 ? col4.y : col4.z);
-              const float Ti = T / (1.f - alpha);  // transmittance in front of this entry
+              const float Ti = __fdividef(T, 1.f - alpha);  // transmittance in front of this entry
               const float dcol = alpha * Ti * G;
               v[4] = ch == 0 ? dcol : 0.f;
               v[5] = ch == 1 ? dcol : 0.f;
@@ -298,13 +303,13 @@ __global__ void __launch_bounds__(256) k_blend_backward(PanelGeom g, BlendArgs a
                 const float dmx = dpower * (co.x * dx + co.y * dy);
                 const float dmy = dpower * (co.y * dx + co.z * dy);
                 if (slot == v0) {
-                  v[7] = dmx;
-                  v[8] = dmy;
+                  v[8] = dmx;
+                  v[9] = dmy;
                 } else if (slot == v1) {
-                  v[9] = dmx;
-                  v[10] = dmy;
+                  v[10] = dmx;
+                  v[11] = dmy;
                 } else {
-                  float* gm = reinterpret_cast<float*>(&s_gmean[slot * NB + gi]);
+                  float* gm = gr.grad_means2d + 2 * (((size_t)k * a.M + s_gid[gi]) * C + slot);
                   atomicAdd(gm + 0, dmx);
                   atomicAdd(gm + 1, dmy);
                 }
@@ -312,18 +317,18 @@ __global__ void __launch_bounds__(256) k_blend_backward(PanelGeom g, BlendArgs a
             }
           }
           if (!__any_sync(0xffffffffu, any)) continue;
-          // lanes 2i and 2i + 1 end with the warp's sum of v[i]
-          const float sum = warp_transpose_sum16(v, lane);
+          // lanes 2i and 2i + 1 end with the warp's sum of v[i] (v[7] unused)
+          const float sum = warp_transpose_sum<16>(v, lane);
           const int i = lane >> 1;
-          if ((lane & 1) == 0 && i < 11 && sum != 0.f) {
-            float* dst;
-            if (i < 4)
-              dst = reinterpret_cast<float*>(&s_gco[gi]) + i;
-            else if (i < 7)
-              dst = reinterpret_cast<float*>(&s_gcol[gi]) + (i - 4);
-            else
-              dst = reinterpret_cast<float*>(&s_gmean[(i < 9 ? v0 : v1) * NB + gi]) + ((i - 7) & 1);
-            atomicAdd(dst, sum);
+          if ((lane & 1) == 0 && i < 12 && sum != 0.f) {
+            if (i < 4) {
+              atomicAdd(reinterpret_cast<float*>(&s_gco[gi]) + i, sum);
+            } else if (i < 7) {
+              atomicAdd(reinterpret_cast<float*>(&s_gcol[gi]) + (i - 4), sum);
+            } else if (i >= 8) {
+              const int vv = i < 10 ? v0 : v1;
+              atomicAdd(gr.grad_means2d + 2 * (((size_t)k * a.M + s_gid[gi]) * C + vv) + (i & 1), sum);
+            }
           }
         }
       }
@@ -556,9 +561,10 @@ cudaError_t launch_blend_backward(const PanelGeom& g, const BlendArgs& a, const 
   const int need = a.max_segment > 0 ? a.max_segment : 1;
   const int block = min(256, ((need + 31) / 32) * 32);
   const int nw = block / 32;
-  const size_t smem = (size_t)block * (4 * sizeof(float4) + 2 * g.C * sizeof(float2) + 2 * sizeof(uint32_t)) +
-                      (((size_t)g.C * block + 1) & ~(size_t)1) * sizeof(uint16_t) +
-                      (size_t)g.C * (nw + 1) * sizeof(int);
+  // the per-view lists are only needed to re-blend (no kept state)
+  const size_t smem = (size_t)block * (4 * sizeof(float4) + g.C * sizeof(float2) + 2 * sizeof(uint32_t)) +
+                      (a.keep ? 0 : (((size_t)g.C * block + 1) & ~(size_t)1) * sizeof(uint16_t) +
+                                        (size_t)g.C * (nw + 1) * sizeof(int));
   const unsigned grid = (unsigned)((int64_t)g.K * g.T);
   if (a.keep) {
     if (smem > 48 * 1024)
