@@ -246,7 +246,12 @@ LFD_API int lfd_render_fullframe(lfd_plan *plan, const lfd_gaussians *g, const l
 /* End-to-end variant for callers holding HOST buffers: the Gaussians in g
  * and out_rgb are host pointers (pinned memory gives the fastest copies). The
  * call copies the inputs to plan-owned device memory, renders, copies the
- * image back and returns once it is in out_rgb. */
+ * image back and returns once it is in out_rgb (or, on an error, once every
+ * copy it queued has finished). The copies run on a plan-owned transfer
+ * stream: the Gaussians go up in four chunks, each projected as it lands,
+ * and the remapped blend runs in four bands of tile rows on plan-owned
+ * streams forked from `stream`, each band's rows copied back as soon as the
+ * band is done. The image equals lfd_render's bit for bit. */
 LFD_API int lfd_render_host(lfd_plan *plan, const lfd_gaussians *g_host,
                     const lfd_camera *cams, int32_t num_cams, float *out_rgb_host,
                     void *stream, lfd_stats *stats);

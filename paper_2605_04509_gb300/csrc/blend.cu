@@ -247,8 +247,9 @@ template <int R, bool COUNT>
 __global__ void __launch_bounds__(256) k_blend(PanelGeom g, BlendArgs a) {
   extern __shared__ float4 smem[];
   if (a.P_dev && *a.P_dev > a.P_cap) return;  // capacity overflow: leave the image
-  const int k = blockIdx.x / g.T;
-  const int t = blockIdx.x - k * g.T;
+  const int nt = a.t_end - a.t_begin;
+  const int k = blockIdx.x / nt;
+  const int t = a.t_begin + (blockIdx.x - k * nt);
   blend_run<R, COUNT>(g, a, k, t, a.ranges[(size_t)t * g.K + k], smem);
 }
 
@@ -285,7 +286,7 @@ size_t blend_smem_bytes(int C, int block) {
 template <int R>
 cudaError_t launch_r(const PanelGeom& g, const BlendArgs& a, int block, cudaStream_t s) {
   const size_t smem = blend_smem_bytes(g.C, block);
-  const unsigned grid = (unsigned)((int64_t)g.K * g.T);
+  const unsigned grid = (unsigned)((int64_t)g.K * (a.t_end - a.t_begin));
   if (a.eval_counter) {
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(k_blend<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -354,8 +355,11 @@ cudaError_t launch_blend_batch(const BatchBlendArgs& b, int max_segment, int C_m
   }
 }
 
-cudaError_t launch_blend(const PanelGeom& g, const BlendArgs& a, cudaStream_t s) {
-  if ((int64_t)g.K * g.T == 0) return cudaSuccess;
+cudaError_t launch_blend(const PanelGeom& g, const BlendArgs& args, cudaStream_t s) {
+  BlendArgs a = args;
+  if (a.t_end < 0 || a.t_end > g.T) a.t_end = g.T;
+  if (a.t_begin < 0) a.t_begin = 0;
+  if (g.K == 0 || a.t_end <= a.t_begin) return cudaSuccess;
   const int need = a.max_segment > 0 ? a.max_segment : 1;
   const int R = choose_r(need, a.subpixels_per_thread);
   int block = (need + R - 1) / R;

@@ -81,6 +81,23 @@ bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 }  // namespace
 
+namespace {
+// Transfers of lfd_render_host, overlapped with the frame's kernels: the
+// Gaussians go up in kHostChunks chunks on a transfer stream and each chunk
+// is projected as soon as it has landed; the remapped blend runs in
+// kHostBands bands of tile rows, launched on streams of their own so that
+// each band's last blocks share the GPU with the next band's first ones, and
+// each band's image rows go back as soon as the band is done.
+constexpr int kHostChunks = 4;
+constexpr int kHostBands = 4;
+struct HostIO {
+  const void* src[5];   // host attribute arrays
+  void* dst[5];         // their device copies
+  size_t elem_bytes[5];  // bytes per Gaussian of each array
+  float* out_host;      // host image [H][W][3]
+};
+}  // namespace
+
 struct lfd_plan {
   lfd_panel panel;
   lfd_opts opts;
@@ -105,6 +122,10 @@ struct lfd_plan {
   DevBuf image;       // device image for lfd_render_host
   DevBuf g_means2d, g_conic, g_color, g_opac;  // backward scratch
   DevBuf keep;  // LFD_FLAG_KEEP_BLEND_STATE: [T][cap] stop index, final T
+  // lfd_render_host: transfer stream and its events (created on first use)
+  cudaStream_t io_stream = nullptr;
+  cudaStream_t band_stream[kHostBands] = {};
+  cudaEvent_t io_ev[2 + kHostChunks + kHostBands] = {};
   unsigned long long* h_small = nullptr;  // pinned
   // last frame
   int64_t last_P = -1;
@@ -240,6 +261,11 @@ void lfd_plan_destroy(lfd_plan* p) {
   for (auto& set : p->ev)
     for (cudaEvent_t& e : set)
       if (e) cudaEventDestroy(e);
+  for (cudaEvent_t& e : p->io_ev)
+    if (e) cudaEventDestroy(e);
+  if (p->io_stream) cudaStreamDestroy(p->io_stream);
+  for (cudaStream_t& b : p->band_stream)
+    if (b) cudaStreamDestroy(b);
   delete p;
 }
 
@@ -420,8 +446,12 @@ static int fill_cams(const lfd_plan* p, const lfd_camera* cams, int32_t num_cams
   return LFD_OK;
 }
 
-int lfd_project(lfd_plan* p, const lfd_gaussians* gs, const lfd_camera* cams, int32_t num_cams,
-                float* means2d, float* conic_opacity, float* color_tau, float* depth, void* stream) {
+// Projection of every Gaussian; with io, the attributes are first copied from
+// the host in chunks on the transfer stream, each chunk projected after it
+// has landed.
+static int project_impl(lfd_plan* p, const lfd_gaussians* gs, const lfd_camera* cams,
+                        int32_t num_cams, float* means2d, float* conic_opacity, float* color_tau,
+                        float* depth, void* stream, const HostIO* io) {
   if (!p) return fail(LFD_ERR_INVALID, "NULL plan");
   int rc = check_gaussians(p, gs);
   if (rc != LFD_OK) return rc;
@@ -448,17 +478,46 @@ int lfd_project(lfd_plan* p, const lfd_gaussians* gs, const lfd_camera* cams, in
     a.conic_opacity = conic_opacity;
     a.color_tau = color_tau;
     a.depth = depth;
-    cudaError_t e = launch_project(p->g, *t, a, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (!io) {
+      e = launch_project(p->g, *t, a, s);
+    } else {
+      // the transfer stream starts after the work already queued on s
+      e = cudaEventRecord(p->io_ev[0], s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(p->io_stream, p->io_ev[0], 0);
+      const int64_t M = gs->count;
+      for (int c = 0; c < kHostChunks && e == cudaSuccess; ++c) {
+        const int64_t m0 = M * c / kHostChunks, m1 = M * (c + 1) / kHostChunks;
+        if (m1 == m0) continue;
+        for (int b = 0; b < 5 && e == cudaSuccess; ++b)
+          e = cudaMemcpyAsync(static_cast<char*>(io->dst[b]) + m0 * io->elem_bytes[b],
+                              static_cast<const char*>(io->src[b]) + m0 * io->elem_bytes[b],
+                              (size_t)(m1 - m0) * io->elem_bytes[b], cudaMemcpyHostToDevice, p->io_stream);
+        if (e == cudaSuccess) e = cudaEventRecord(p->io_ev[1 + c], p->io_stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->io_ev[1 + c], 0);
+        a.m_begin = m0;
+        a.m_end = m1;
+        if (e == cudaSuccess) e = launch_project(p->g, *t, a, s);
+      }
+    }
     if (e != cudaSuccess) rc = fail_cuda(e, "project");
   }
   delete t;
   return rc;
 }
 
+int lfd_project(lfd_plan* p, const lfd_gaussians* gs, const lfd_camera* cams, int32_t num_cams,
+                float* means2d, float* conic_opacity, float* color_tau, float* depth, void* stream) {
+  return project_impl(p, gs, cams, num_cams, means2d, conic_opacity, color_tau, depth, stream, nullptr);
+}
+
+// Stages 2-4 from projected attributes. With io, the image also goes back to
+// io->out_host on the transfer stream (band by band for the remapped blend).
 static int render_projected_impl(lfd_plan* p, int64_t M, const float* means2d,
                                  const float* conic_opacity, const float* color_tau,
                                  const float* depth, float* out_rgb, void* stream, lfd_stats* stats,
-                                 bool projected_here) {
+                                 bool projected_here, const HostIO* io = nullptr) {
   if (!p) return fail(LFD_ERR_INVALID, "NULL plan");
   const PanelGeom& g = p->g;
   cudaStream_t s = (cudaStream_t)stream;
@@ -584,12 +643,49 @@ static int render_projected_impl(lfd_plan* p, int64_t M, const float* means2d,
   ba.subpixels_per_thread = p->opts.subpixels_per_thread;
   const bool kept = (p->flags & LFD_FLAG_KEEP_BLEND_STATE) && p->opts.remap && !p->fullframe;
   ba.keep = kept ? p->keep.as<uint2>() : nullptr;
-  if (p->fullframe)
+  const size_t row_floats = (size_t)g.W * 3;
+  if (p->fullframe) {
     LFD_CUDA(launch_blend_fullframe(g, ba, s));
-  else if (p->opts.remap)
+  } else if (p->opts.remap && io) {
+    // bands of tile rows, forked from s and joined back into it
+    cudaEvent_t ev_fork = p->io_ev[1 + kHostChunks + kHostBands];
+    LFD_CUDA(cudaEventRecord(ev_fork, s));
+    int done = 0;
+    for (int b = 0; b < kHostBands; ++b) {
+      const int ty0 = done, ty1 = g.TY * (b + 1) / kHostBands;
+      cudaStream_t sb = p->band_stream[b];
+      cudaEvent_t ev_b = p->io_ev[1 + kHostChunks + b];
+      LFD_CUDA(cudaStreamWaitEvent(sb, ev_fork, 0));
+      if (ty1 > ty0) {
+        done = ty1;
+        ba.t_begin = ty0 * g.TX;
+        ba.t_end = ty1 * g.TX;
+        LFD_CUDA(launch_blend(g, ba, sb));
+      }
+      LFD_CUDA(cudaEventRecord(ev_b, sb));
+      LFD_CUDA(cudaStreamWaitEvent(s, ev_b, 0));
+      if (ty1 > ty0) {
+        const int y0 = ty0 * g.TH, y1 = min(ty1 * g.TH, g.H);
+        LFD_CUDA(cudaStreamWaitEvent(p->io_stream, ev_b, 0));
+        LFD_CUDA(cudaMemcpyAsync(io->out_host + (size_t)y0 * row_floats, out_rgb + (size_t)y0 * row_floats,
+                                 (size_t)(y1 - y0) * row_floats * sizeof(float), cudaMemcpyDeviceToHost,
+                                 p->io_stream));
+      }
+    }
+    ba.t_begin = 0;
+    ba.t_end = -1;
+  } else if (p->opts.remap) {
     LFD_CUDA(launch_blend(g, ba, s));
-  else
+  } else {
     LFD_CUDA(launch_blend_raster(g, ba, s));
+  }
+  if (io && (p->fullframe || !p->opts.remap)) {
+    cudaEvent_t ev_b = p->io_ev[1 + kHostChunks];
+    LFD_CUDA(cudaEventRecord(ev_b, s));
+    LFD_CUDA(cudaStreamWaitEvent(p->io_stream, ev_b, 0));
+    LFD_CUDA(cudaMemcpyAsync(io->out_host, out_rgb, (size_t)g.H * row_floats * sizeof(float),
+                             cudaMemcpyDeviceToHost, p->io_stream));
+  }
   if (timing) {
     LFD_CUDA(cudaEventRecord(ev[4], s));
     p->ev_pending[es] = true;
@@ -637,8 +733,8 @@ int lfd_render_projected(lfd_plan* p, int64_t M, const float* means2d, const flo
                                stats, false);
 }
 
-int lfd_render(lfd_plan* p, const lfd_gaussians* gs, const lfd_camera* cams, int32_t num_cams,
-               float* out_rgb, void* stream, lfd_stats* stats) {
+static int render_impl(lfd_plan* p, const lfd_gaussians* gs, const lfd_camera* cams, int32_t num_cams,
+                       float* out_rgb, void* stream, lfd_stats* stats, const HostIO* io) {
   if (!p) return fail(LFD_ERR_INVALID, "NULL plan");
   int rc = check_gaussians(p, gs);
   if (rc != LFD_OK) return rc;
@@ -652,12 +748,17 @@ int lfd_render(lfd_plan* p, const lfd_gaussians* gs, const lfd_camera* cams, int
   cudaStream_t s = (cudaStream_t)stream;
   const bool timing = (p->flags & LFD_FLAG_STAGE_TIMING) != 0;
   if (timing) LFD_CUDA(cudaEventRecord(p->ev[p->ev_set][0], s));
-  rc = lfd_project(p, gs, cams, num_cams, p->proj_means.as<float>(), p->proj_co.as<float>(),
-                   p->proj_ct.as<float>(), p->proj_depth.as<float>(), stream);
+  rc = project_impl(p, gs, cams, num_cams, p->proj_means.as<float>(), p->proj_co.as<float>(),
+                    p->proj_ct.as<float>(), p->proj_depth.as<float>(), stream, io);
   if (rc != LFD_OK) return rc;
   return render_projected_impl(p, M, p->proj_means.as<float>(), p->proj_co.as<float>(),
                                p->proj_ct.as<float>(), p->proj_depth.as<float>(), out_rgb, stream,
-                               stats, true);
+                               stats, true, io);
+}
+
+int lfd_render(lfd_plan* p, const lfd_gaussians* gs, const lfd_camera* cams, int32_t num_cams,
+               float* out_rgb, void* stream, lfd_stats* stats) {
+  return render_impl(p, gs, cams, num_cams, out_rgb, stream, stats, nullptr);
 }
 
 int lfd_render_backward(lfd_plan* p, const lfd_gaussians* gs, const lfd_camera* cams,
@@ -765,30 +866,42 @@ int lfd_render_host(lfd_plan* p, const lfd_gaussians* gh, const lfd_camera* cams
   if (M < 0 || gh->sh_degree < 0 || gh->sh_degree > 3) return fail(LFD_ERR_INVALID, "bad Gaussian set");
   const int ncoef = (gh->sh_degree + 1) * (gh->sh_degree + 1);
   const size_t es = gh->attr_dtype == LFD_DTYPE_F32 ? 4 : 2;
-  const size_t bytes[5] = {(size_t)M * 12, (size_t)M * 3 * es, (size_t)M * 4 * es, (size_t)M * es,
-                           (size_t)M * ncoef * 3 * es};
+  HostIO io;
+  const size_t eb[5] = {12, 3 * es, 4 * es, es, (size_t)ncoef * 3 * es};
   const void* src[5] = {gh->means, gh->scales, gh->quats, gh->opacities, gh->sh};
-  cudaStream_t s = (cudaStream_t)stream;
   int rc;
   for (int b = 0; b < 5; ++b) {
-    if ((rc = p->host_in[b].ensure(bytes[b] + 16)) != LFD_OK) return rc;
-    if (M > 0) {
-      if (!src[b]) return fail(LFD_ERR_INVALID, "NULL Gaussian attribute");
-      LFD_CUDA(cudaMemcpyAsync(p->host_in[b].p, src[b], bytes[b], cudaMemcpyHostToDevice, s));
-    }
+    if ((rc = p->host_in[b].ensure((size_t)M * eb[b] + 16)) != LFD_OK) return rc;
+    if (M > 0 && !src[b]) return fail(LFD_ERR_INVALID, "NULL Gaussian attribute");
+    io.src[b] = src[b];
+    io.dst[b] = p->host_in[b].p;
+    io.elem_bytes[b] = eb[b];
   }
+  io.out_host = out_rgb_host;
   const size_t out_bytes = (size_t)p->g.W * p->g.H * 3 * sizeof(float);
   if ((rc = p->image.ensure(out_bytes)) != LFD_OK) return rc;
+  if (!p->io_stream) {  // created last: set once everything else exists
+    for (cudaStream_t& b : p->band_stream)
+      if (!b) LFD_CUDA(cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking));
+    for (cudaEvent_t& e : p->io_ev)
+      if (!e) LFD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    LFD_CUDA(cudaStreamCreateWithFlags(&p->io_stream, cudaStreamNonBlocking));
+  }
   lfd_gaussians gd = *gh;
   gd.means = p->host_in[0].as<float>();
   gd.scales = p->host_in[1].p;
   gd.quats = p->host_in[2].p;
   gd.opacities = p->host_in[3].p;
   gd.sh = p->host_in[4].p;
-  rc = lfd_render(p, &gd, cams, num_cams, p->image.as<float>(), stream, stats);
+  cudaStream_t s = (cudaStream_t)stream;
+  rc = render_impl(p, &gd, cams, num_cams, p->image.as<float>(), stream, stats, &io);
+  // copies already queued read or write the caller's host buffers: let them
+  // finish before returning, whatever the outcome
+  const cudaError_t e1 = cudaStreamSynchronize(p->io_stream);
+  const cudaError_t e2 = cudaStreamSynchronize(s);
   if (rc != LFD_OK) return rc;
-  LFD_CUDA(cudaMemcpyAsync(out_rgb_host, p->image.p, out_bytes, cudaMemcpyDeviceToHost, s));
-  LFD_CUDA(cudaStreamSynchronize(s));
+  if (e1 != cudaSuccess) return fail_cuda(e1, "host transfers");
+  if (e2 != cudaSuccess) return fail_cuda(e2, "render");
   return LFD_OK;
 }
 

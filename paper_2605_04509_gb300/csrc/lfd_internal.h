@@ -54,6 +54,9 @@ struct ProjectArgs {
   float* conic_opacity;  // [K][M][4]
   float* color_tau;      // [K][M][4]
   float* depth;          // [K][M]
+  // Gaussians [m_begin, m_end) only (m_end < 0: to M); outputs keep stride M
+  int64_t m_begin = 0;
+  int64_t m_end = -1;
 };
 cudaError_t launch_project(const PanelGeom& g, const CamTable& cams, const ProjectArgs& a,
                            cudaStream_t s);
@@ -229,6 +232,9 @@ struct BlendArgs {
   // walk stopped (the range end if it never saturated) and the bits of its
   // final transmittance; written by the remapped blend, read by the backward
   uint2* keep = nullptr;
+  // remapped blend: tiles [t_begin, t_end) only (t_end < 0: to T)
+  int t_begin = 0;
+  int t_end = -1;
 };
 cudaError_t launch_blend(const PanelGeom& g, const BlendArgs& a, cudaStream_t s);
 

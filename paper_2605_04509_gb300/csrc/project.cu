@@ -51,8 +51,8 @@ __device__ __forceinline__ float depth_rn(const float* c, float x, float y, floa
 
 template <typename A>
 __global__ void __launch_bounds__(128) k_project(PanelGeom g, CamTable cams, ProjectArgs a) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.M) return;
+  const int64_t i = a.m_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.m_end) return;
   const A* quats = reinterpret_cast<const A*>(a.quats);
   const A* scales = reinterpret_cast<const A*>(a.scales);
   const A* opac = reinterpret_cast<const A*>(a.opac);
@@ -189,11 +189,14 @@ __global__ void __launch_bounds__(128) k_project(PanelGeom g, CamTable cams, Pro
 
 }  // namespace
 
-cudaError_t launch_project(const PanelGeom& g, const CamTable& cams, const ProjectArgs& a,
+cudaError_t launch_project(const PanelGeom& g, const CamTable& cams, const ProjectArgs& args,
                            cudaStream_t s) {
-  if (a.M == 0) return cudaSuccess;
+  ProjectArgs a = args;
+  if (a.m_end < 0 || a.m_end > a.M) a.m_end = a.M;
+  if (a.m_begin < 0) a.m_begin = 0;
+  if (a.m_end <= a.m_begin) return cudaSuccess;
   const int threads = 128;
-  const int64_t blocks = (a.M + threads - 1) / threads;
+  const int64_t blocks = (a.m_end - a.m_begin + threads - 1) / threads;
   if (a.attr_dtype == LFD_DTYPE_F16)
     k_project<__half><<<(unsigned)blocks, threads, 0, s>>>(g, cams, a);
   else if (a.attr_dtype == LFD_DTYPE_BF16)

@@ -5,6 +5,8 @@ Eq. 11 keys, the sorted list and the range table. Tolerance (clamped [0, 1]
 images): max |err| <= 2e-3 and at most 0.1 % of subpixels off by more than
 1/255, against the FP64 oracle.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -322,12 +324,34 @@ def test_deterministic(tiny):
     plan.close()
 
 
-def test_host_entry_point_matches_device(tiny):
+@pytest.mark.parametrize("remap", [True, False])
+def test_host_entry_point_matches_device(tiny, remap):
+    # the host entry point copies the Gaussians up in chunks, projecting each
+    # as it lands, and (remapped blend) the image back in bands of tile rows
     w, scene, cams = tiny
-    plan = lfd.Plan(w.panel, views_per_cluster=8)
+    plan = lfd.Plan(w.panel, views_per_cluster=8, remap=remap)
     dev, _ = plan.render(lfd.scene_to_device(scene), cams)
     host_scene = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in scene.items()}
     out = torch.empty(dev.shape, dtype=torch.float32).pin_memory()
+    plan.render_host(host_scene, cams, out)
+    assert torch.equal(out, dev.cpu())
+    plan.close()
+
+
+@pytest.mark.parametrize("height,count", [(32, 2001), (144, 3), (16, 0)])
+def test_host_entry_point_ragged(height, count):
+    # fewer tile rows than bands, Gaussian counts not divisible by the chunk
+    # count (or below it, or zero), FP16 attributes from pageable memory
+    panel = synth.Panel(96, height, 8, math.tan(0.2), 4.5, 0.0)
+    rig = synth.Rig(8, 40.0, 4.0, 50.0)
+    cams = synth.arc_cameras(rig, panel.width, panel.height)
+    scene = synth.uniform_scene(count, 9, half_extent=0.8)
+    plan = lfd.Plan(panel, views_per_cluster=8)
+    dev, _ = plan.render(lfd.scene_to_device(scene, attr_dtype=torch.float16), cams)
+    host_scene = {k: (torch.from_numpy(np.ascontiguousarray(v)) if k == "means"
+                      else torch.from_numpy(np.ascontiguousarray(v)).to(torch.float16))
+                  for k, v in scene.items()}
+    out = torch.full(dev.shape, -1.0, dtype=torch.float32)
     plan.render_host(host_scene, cams, out)
     assert torch.equal(out, dev.cpu())
     plan.close()
