@@ -9,7 +9,7 @@
 // while it ranks one tile, the bulk-copy engine (cp.async.bulk, completion on
 // an mbarrier) fetches the block's next tile into the other half of a double
 // buffer in shared memory. Inside a tile each warp ranks its items with
-// ballot peer masks in (round, lane) order and per-warp digit counters, the
+// warp-match peer masks in (round, lane) order and per-warp digit counters, the
 // warps' counters are prefixed, and the items are scattered through shared
 // memory so that each digit's run is written with consecutive addresses.
 // No block waits on another block. The item count may be given on the device
@@ -188,18 +188,10 @@ __global__ void __launch_bounds__(kSortThreads)
   }
 }
 
-// Peer mask of the lanes holding the same digit, from one ballot per digit
-// bit (and one for validity).
+// Peer mask of the lanes holding the same digit (invalid lanes form a group
+// of their own): one warp match instead of a ballot per digit bit.
 __device__ __forceinline__ unsigned digit_peers(int d, bool valid) {
-  unsigned m = __ballot_sync(0xffffffffu, valid);
-  m = valid ? m : ~m;
-#pragma unroll
-  for (int b = 0; b < kRadixBits; ++b) {
-    const bool bit = (d >> b) & 1;
-    const unsigned bb = __ballot_sync(0xffffffffu, bit);
-    m &= bit ? bb : ~bb;
-  }
-  return m;
+  return __match_any_sync(0xffffffffu, valid ? d : -1);
 }
 
 // Stable scatter of one pass. Block b handles tiles b, b + G, b + 2G, ...
