@@ -40,7 +40,8 @@ WORKLOAD_TEXT = ("paper4k: 1M Gaussians (64-blob mixture, radius 10), 45 views o
                  "|V_k|=8 (K=6), SH degree 3, FP32")
 # tile shapes the default run's autotuner tries (paper_2605_04509_gb300.autotune)
 AUTOTUNE_TILES = ((16, 16), (24, 16), (32, 16), (32, 8))
-# FP32 peak of the blend's pipe: 152 SMs x 128 FP32 lanes x 2070 MHz max SM clock
+# FP32 peak of the blend's pipe: SMs (queried; 152 on GB300) x 128 FP32 lanes x
+# 2070 MHz max SM clock; exp2 pipe: 16 lanes per SM
 SMS, FP32_LANES, SM_MAX_MHZ, MUFU_LANES = 152, 128, 2070.0, 16
 # algorithmic FP32 operations per visited (subpixel, Gaussian) evaluation:
 # 2 sub (offset) + 3 mul/fma (quadratic form) + 1 mul (o * 2^x) + 1 min +
@@ -321,6 +322,9 @@ def run_ours(args):
     stages = plan.stage_totals(reset=True)
     plan.set_flags(0)
     torch.cuda.synchronize(device)
+    # the blend's arithmetic ceilings measured on this GPU (untimed)
+    probe = lfd.measure_alu_peaks(stream)
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
 
     sampler = ClockSampler(gpu_id_for(torch, local))
     barrier(world, device)
@@ -346,16 +350,22 @@ def run_ours(args):
     n_frames_staged = max(stages["frames"], 1)
     blend_ms = stages["ms_blend"] / n_frames_staged
     achieved = E * OPS_PER_EVAL / (blend_ms * 1e-3) / 1e12
-    peak = SMS * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12
-    ex2_frac = E / (blend_ms * 1e-3) / (SMS * MUFU_LANES * SM_MAX_MHZ * 1e6)
+    peak = sms * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12
+    ex2_frac = E / (blend_ms * 1e-3) / (sms * MUFU_LANES * SM_MAX_MHZ * 1e6)
     traffic = blend_traffic_bytes(tile_text) if (args.workload == "paper4k" and not args.gaussians
                                                  and C == 8) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOP/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": "k_blend",
                 "units": f"E = {E} visited (subpixel, Gaussian) evaluations per launch x "
-                         f"{OPS_PER_EVAL} FP32 ops; peak = 152 SMs x 128 FP32 lanes x 2070 MHz "
-                         f"(of fallback unit counts; the measured peaks file has no FP32 figure)",
-                "blend_ms": blend_ms, "ex2_pipe_frac": ex2_frac}
+                         f"{OPS_PER_EVAL} FP32 ops; peak = {sms} SMs (queried) x 128 FP32 lanes x "
+                         f"2070 MHz (derived from unit counts and the maximum clock; the measured "
+                         f"peaks file has no FP32 figure)",
+                "blend_ms": blend_ms, "ex2_pipe_frac": ex2_frac,
+                "probe": {"fp32_tops": probe["fp32_ops_per_s"] / 1e12,
+                          "ex2_gps": probe["ex2_per_s"] / 1e9,
+                          "frac_of_fp32_probe": achieved / (probe["fp32_ops_per_s"] / 1e12),
+                          "what": "lfd_measure_alu_peaks on this GPU before the timed region: "
+                                  "independent FMA chains and ex2.approx chains over every SM"}}
     line = {
         "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,

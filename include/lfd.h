@@ -372,6 +372,16 @@ LFD_API int lfd_get_stage_totals(lfd_plan *plan, lfd_stage_times *out, int32_t r
  * and frees a 4-byte flag. */
 LFD_API int lfd_selftest_wait_timeout(void *stream);
 
+/* Measured ceilings of the blend's arithmetic on the current device (not in
+ * the paper; the roofline of Eq. 9-10's per-evaluation work): one kernel of
+ * independent FP32 fused multiply-add chains and one of independent
+ * ex2.approx chains, each over every SM after an untimed round. Writes FP32
+ * lane operations per second (an FMA counts as one) and exp2 evaluations per
+ * second to the two host doubles. Synchronises the stream; allocates and
+ * frees a small device buffer. LFD_ERR_INVALID for NULL outputs,
+ * LFD_ERR_OOM, LFD_ERR_CUDA. */
+LFD_API int lfd_measure_alu_peaks(double *fp32_ops_per_s, double *ex2_per_s, void *stream);
+
 /* Number of CUDA kernels this library has launched in the process so far. */
 LFD_API uint64_t lfd_kernel_launches(void);
 

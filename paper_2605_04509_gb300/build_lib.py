@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "liblfd.so")
 SOURCES = ["lfd_api.cu", "plan_kernels.cu", "project.cu", "binning.cu", "sort.cu", "blend.cu",
-           "blend_raster.cu", "blend_fullframe.cu", "backward.cu", "noalloc.cu", "batch.cu"]
+           "blend_raster.cu", "blend_fullframe.cu", "backward.cu", "noalloc.cu", "batch.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

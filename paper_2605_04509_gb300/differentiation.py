@@ -11,7 +11,9 @@ transmittance and stop position) + loss + backward (lfd_render_backward: each
 (tile, cluster) run walked back to front from the kept state, then the 3DGS
 projection chain) through lfd.render_autograd, then one plain gradient step
 on the means. Prints steps/s, the forward and backward times, the loss
-before and after, and the gradient norms per parameter group. The gradients
+before and after, and the gradient norms per parameter group; then the same
+for the backward that re-blends each list first (nothing kept by the
+forward), under "replay". The gradients
 themselves are checked against the FP64 autograd oracle (itself pinned to
 finite differences) by tests/test_gpu_backward.py.
 """
@@ -37,48 +39,60 @@ def run(steps: int = 10, lr: float = 1e-4):
     plan = lfd.Plan(w.panel, views_per_cluster=8)
     target, _ = plan.render(lfd.scene_to_device(moved), cams)
     target = target.clone()
-    leaves = {k: v.clone().requires_grad_(True) for k, v in lfd.scene_to_device(scene).items()}
     keys = ("means", "scales", "quats", "opacities", "sh")
 
-    def step(apply: bool):
-        for v in leaves.values():
-            v.grad = None
-        img = lfd.render_autograd(plan, cams, *(leaves[k] for k in keys))
-        loss = ((img - target) ** 2).sum()
-        loss.backward()
-        if apply:
-            with torch.no_grad():
-                leaves["means"] -= lr * leaves["means"].grad
-        return loss
+    def optimise(keep_state: bool):
+        """`steps` timed optimisation steps from the unperturbed scene."""
+        leaves = {k: v.clone().requires_grad_(True) for k, v in lfd.scene_to_device(scene).items()}
 
-    loss0 = float(step(False))
-    for _ in range(2):
-        step(False)
-    torch.cuda.synchronize()
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    e[0].record()
-    for _ in range(steps):
-        loss = step(True)
-    e[1].record()
-    torch.cuda.synchronize()
-    ms_step = e[0].elapsed_time(e[1]) / steps
-    # forward alone, for the split
-    f = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    with torch.no_grad():
-        scene_now = {k: v.detach() for k, v in leaves.items()}
-        f[0].record()
+        def step(apply: bool):
+            for v in leaves.values():
+                v.grad = None
+            img = lfd.render_autograd(plan, cams, *(leaves[k] for k in keys), keep_state=keep_state)
+            loss = ((img - target) ** 2).sum()
+            loss.backward()
+            if apply:
+                with torch.no_grad():
+                    leaves["means"] -= lr * leaves["means"].grad
+            return loss
+
+        loss0 = float(step(False).detach())
+        for _ in range(2):
+            step(False)
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record()
         for _ in range(steps):
-            plan.render(scene_now, cams)
-        f[1].record()
-    torch.cuda.synchronize()
-    ms_fwd = f[0].elapsed_time(f[1]) / steps
+            loss = step(True)
+        e[1].record()
+        torch.cuda.synchronize()
+        ms_step = e[0].elapsed_time(e[1]) / steps
+        # forward alone (same flags), for the split
+        f = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        with torch.no_grad():
+            scene_now = {k: v.detach() for k, v in leaves.items()}
+            f[0].record()
+            for _ in range(steps):
+                plan.render(scene_now, cams)
+            f[1].record()
+        torch.cuda.synchronize()
+        ms_fwd = f[0].elapsed_time(f[1]) / steps
+        return {"ms_per_step": ms_step, "steps_per_s": 1000.0 / ms_step, "ms_forward": ms_fwd,
+                "ms_backward_and_loss": ms_step - ms_fwd, "loss_first": loss0,
+                "loss_last": float(loss.detach()),
+                "grad_norms": {k: float(leaves[k].grad.norm()) for k in keys}}
+
+    kept = optimise(True)
+    replay = optimise(False)
     line = {
         "workload": "diff1080: 500k Gaussians, 24 views, 1920x1080 panel, |V_k| = 8, L2 loss to a "
                     "target rendered from means + N(0, 0.01)",
-        "steps": steps, "ms_per_step": ms_step, "steps_per_s": 1000.0 / ms_step,
-        "ms_forward": ms_fwd, "ms_backward_and_loss": ms_step - ms_fwd,
-        "loss_first": loss0, "loss_last": float(loss),
-        "grad_norms": {k: float(leaves[k].grad.norm()) for k in keys},
+        "steps": steps,
+        **kept,
+        "replay": {k: replay[k] for k in ("ms_per_step", "steps_per_s", "ms_forward",
+                                          "ms_backward_and_loss", "loss_last")},
+        "replay_note": "backward re-blends each (tile, cluster) list to find each subpixel's final "
+                       "transmittance instead of reading the 8 bytes per subpixel the forward kept",
     }
     print(json.dumps(line), flush=True)
     plan.close()

@@ -124,6 +124,7 @@ def load() -> ct.CDLL:
             "lfd_batch_render": ([_P, _P, _P, _P, _P], ct.c_int),
             "lfd_batch_status": ([_P, ct.POINTER(ct.c_int64)], ct.c_int),
             "lfd_selftest_wait_timeout": ([_P], ct.c_int),
+            "lfd_measure_alu_peaks": ([ct.POINTER(ct.c_double), ct.POINTER(ct.c_double), _P], ct.c_int),
             "lfd_kernel_launches": ([], ct.c_uint64),
             "lfd_status_string": ([ct.c_int], ct.c_char_p),
             "lfd_last_error": ([], ct.c_char_p),
@@ -371,6 +372,13 @@ class Plan:
         return lst[:num_pairs], ranges, (keys[:num_pairs] if with_keys else None)
 
 
+def measure_alu_peaks(stream=None) -> Dict[str, float]:
+    """lfd_measure_alu_peaks: measured FP32 lane operations/s and exp2/s."""
+    f, e = ct.c_double(), ct.c_double()
+    _check(load().lfd_measure_alu_peaks(ct.byref(f), ct.byref(e), _stream_ptr(stream)))
+    return {"fp32_ops_per_s": f.value, "ex2_per_s": e.value}
+
+
 def kernel_launches() -> int:
     """Kernels launched by liblfd in this process so far."""
     return int(load().lfd_kernel_launches())
@@ -389,15 +397,20 @@ def scene_to_device(scene: Dict[str, np.ndarray], device="cuda", attr_dtype=None
     return out
 
 
-def render_autograd(plan: "Plan", cams: np.ndarray, means, scales, quats, opacities, sh):
+def render_autograd(plan: "Plan", cams: np.ndarray, means, scales, quats, opacities, sh,
+                    keep_state: bool = True):
     """Differentiable interlaced render: forward through lfd_render, backward
-    through lfd_render_backward (a torch.autograd.Function). Turns on the
-    plan's FLAG_KEEP_BLEND_STATE so that the backward starts from the
-    forward's per-subpixel state."""
+    through lfd_render_backward (a torch.autograd.Function). keep_state turns
+    on the plan's FLAG_KEEP_BLEND_STATE so that the backward starts from each
+    subpixel's final transmittance and stop position kept by the forward
+    (8 bytes per subpixel); without it (and the flag off) the backward
+    re-blends every (tile, cluster) list first. Either way no per-subpixel
+    list is stored: the backward walks the tile lists again."""
     import torch
 
-    if not plan.flags & FLAG_KEEP_BLEND_STATE:
-        plan.set_flags(plan.flags | FLAG_KEEP_BLEND_STATE)
+    want = (plan.flags | FLAG_KEEP_BLEND_STATE) if keep_state else (plan.flags & ~FLAG_KEEP_BLEND_STATE)
+    if want != plan.flags:
+        plan.set_flags(want)
 
     class _Render(torch.autograd.Function):
         @staticmethod
