@@ -41,8 +41,8 @@ WORKLOAD_TEXT = ("paper4k: 1M Gaussians (64-blob mixture, radius 10), 45 views o
 # tile shapes the default run's autotuner tries (paper_2605_04509_gb300.autotune)
 AUTOTUNE_TILES = ((16, 16), (24, 16), (32, 16), (32, 8))
 # FP32 peak of the blend's pipe: SMs (queried; 152 on GB300) x 128 FP32 lanes x
-# 2070 MHz max SM clock; exp2 pipe: 16 lanes per SM
-SMS, FP32_LANES, SM_MAX_MHZ, MUFU_LANES = 152, 128, 2070.0, 16
+# 2070 MHz max SM clock; the exp2 pipe's rate is taken from the probe
+FP32_LANES, SM_MAX_MHZ = 128, 2070.0
 # algorithmic FP32 operations per visited (subpixel, Gaussian) evaluation:
 # 2 sub (offset) + 3 mul/fma (quadratic form) + 1 mul (o * 2^x) + 1 min +
 # 1 skip compare + 1 fma (T') + 1 compare + 2 (C += c alpha T); plus one exp2
@@ -351,7 +351,7 @@ def run_ours(args):
     blend_ms = stages["ms_blend"] / n_frames_staged
     achieved = E * OPS_PER_EVAL / (blend_ms * 1e-3) / 1e12
     peak = sms * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12
-    ex2_frac = E / (blend_ms * 1e-3) / (sms * MUFU_LANES * SM_MAX_MHZ * 1e6)
+    ex2_frac = E / (blend_ms * 1e-3) / probe["ex2_per_s"]
     traffic = blend_traffic_bytes(tile_text) if (args.workload == "paper4k" and not args.gaussians
                                                  and C == 8) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOP/s",
