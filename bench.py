@@ -43,6 +43,34 @@ AUTOTUNE_TILES = ((16, 16), (24, 16), (32, 16), (32, 8))
 # FP32 peak of the blend's pipe: SMs (queried; 152 on GB300) x 128 FP32 lanes x
 # 2070 MHz max SM clock; the exp2 pipe's rate is taken from the probe
 FP32_LANES, SM_MAX_MHZ = 128, 2070.0
+
+
+def hbm_peak_gbs() -> tuple:
+    """HBM copy bandwidth measured on this machine (MEASURED_PEAKS.json), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "of measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "of fallback"
+
+
+def stage_rooflines(stages_ms, M, K, C, P, gaussian_bytes):
+    """Algorithmic HBM bytes of the three HBM-side stages (each written and
+    read once: a lower bound) over their stage times, against the HBM peak."""
+    peak, which = hbm_peak_gbs()
+    proj = K * M * (16 + 16 + 4 + 8 * C)  # conic+opacity, colour+tau, depth, C means
+    work = {
+        "project": M * gaussian_bytes + proj,   # Gaussians read, projections written
+        "keygen": proj + P * 8,                 # projections read, pairs (key, value) written
+        "sort": P * 8 * 2,                      # pairs read and written once
+    }
+    out = {"bound": "hbm", "peak_gbs": peak, "peak_is": which,
+           "what": "algorithmic bytes / stage time; keygen also runs the exact FP32 tile-bin rule"}
+    for name, b in work.items():
+        ms = stages_ms["ms_" + name]
+        gbs = b / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+        out[name] = {"bytes": int(b), "gbs": gbs, "frac": gbs / peak}
+    return out
 # algorithmic FP32 operations per visited (subpixel, Gaussian) evaluation:
 # 2 sub (offset) + 3 mul/fma (quadratic form) + 1 mul (o * 2^x) + 1 min +
 # 1 skip compare + 1 fma (T') + 1 compare + 2 (C += c alpha T); plus one exp2
@@ -384,6 +412,11 @@ def run_ours(args):
                         "library records around each stage on the frame's stream in the frames right "
                         "before the timed ones; the timed frames run without those events"),
         "roofline": roofline,
+        "stage_roofline": stage_rooflines(
+            {k: stages[k] / n_frames_staged for k in ("ms_project", "ms_keygen", "ms_sort")},
+            M=int(dscene["means"].shape[0]), K=plan.K, C=C, P=P,
+            gaussian_bytes=sum(int(v.numel() * v.element_size()) // max(int(v.shape[0]), 1)
+                               for v in dscene.values())),
         "autotune": autotune,
         "gpu_launches": int(launches),
         "clocks": clocks,
