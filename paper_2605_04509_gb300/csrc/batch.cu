@@ -284,8 +284,7 @@ int lfd_batch_render(lfd_batch* b, const lfd_gaussians* scenes, const lfd_camera
                         b->pair_val[0].as<uint32_t>(), b->pair_val[1].as<uint32_t>(), (int64_t)P,
                         d_small, low, low + b->bit_t, b->radix_tmp.p, &alt, d_err, st));
   const int kb = alt ? 1 : 0;
-  BatchRangeArgs ra;
-  memset(&ra, 0, sizeof(ra));
+  BatchRangeArgs ra{};
   ra.n_scenes = b->n;
   ra.T_max = b->T_max;
   ra.K_glob = b->K_glob;
@@ -298,8 +297,7 @@ int lfd_batch_render(lfd_batch* b, const lfd_gaussians* scenes, const lfd_camera
   B_CUDA(launch_ranges_batch(ra, (int64_t)P, d_small, b->pair_key[kb].as<uint32_t>(),
                              b->ranges.as<uint2>(), st));
   // one persistent blend over every scene's runs
-  BatchBlendArgs ba;
-  memset(&ba, 0, sizeof(ba));
+  BatchBlendArgs ba{};  // zero, with the members' own defaults
   for (int s = 0; s < b->n; ++s) {
     SceneBlend& sc = ba.sc[s];
     sc.g = b->g[s];

@@ -114,3 +114,39 @@ def test_autograd_function_matches_entry_point():
         scale = float(direct[key].abs().max())
         assert err <= 1e-4 * scale, (key, err, scale)
     plan.close()
+
+
+def test_kept_state_in_capacity_mode_under_graph():
+    # the kept blend state is allocated by set_flags, so capacity-mode frames
+    # (no host read-back, no allocation) keep it inside a captured graph too
+    panel, scene, cams, V, target = case(8)
+    s = lfd.scene_to_device(scene)
+    tgt = torch.from_numpy(target.astype(np.float32)).cuda()
+    ref_plan = lfd.Plan(panel, views_per_cluster=8)
+    ref_plan.set_flags(lfd.FLAG_KEEP_BLEND_STATE)
+    want, st = ref_plan.render(s, cams)
+    want = want.clone()
+    ref = ref_plan.backward(s, cams, 2.0 * (want - tgt))
+    plan = lfd.Plan(panel, views_per_cluster=8)
+    plan.set_flags(lfd.FLAG_KEEP_BLEND_STATE)
+    plan.reserve(s["means"].shape[0], 2 * int(st["num_pairs"]) + 16)
+    out = torch.zeros_like(want)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        plan.render(s, cams, out=out)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        plan.render(s, cams, out=out)
+    out.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert plan.status() == int(st["num_pairs"])
+    assert torch.equal(out, want)
+    got = plan.backward(s, cams, 2.0 * (out - tgt))
+    for key in KEYS:
+        err = float((got[key] - ref[key]).abs().max())
+        scale = float(ref[key].abs().max())
+        assert err <= 1e-4 * scale, (key, err, scale)
+    plan.close()
+    ref_plan.close()
