@@ -2,16 +2,18 @@
 // with respect to the Gaussians' means, scales, rotations, opacities and SH
 // coefficients. Not in the paper; it differentiates the same definitions
 // (Eq. 5-6 projection with attribute reuse, Eq. 9-10 blend with the 3DGS
-// rules). No per-subpixel lists are stored by the forward pass: each subpixel
-// re-blends its (tile, cluster) list front to back to find its final
-// transmittance and the entry where it stopped, then walks back to front.
+// rules). No per-subpixel lists are stored by the forward pass. Each
+// subpixel needs its final transmittance and the list entry where it
+// stopped: the forward keeps those 8 bytes per subpixel when asked
+// (LFD_FLAG_KEEP_BLEND_STATE), otherwise the subpixel re-blends its
+// (tile, cluster) list front to back to find them. It then walks the list
+// back to front.
 #include "lfd_internal.h"
 
 namespace lfd {
 namespace {
 
 constexpr float kLog2e = 1.4426950408889634f;
-constexpr float kLn2 = 0.6931471805599453f;
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTMin = 1e-4f;
@@ -364,12 +366,10 @@ __global__ void __launch_bounds__(128) k_project_backward(PanelGeom g, CamTable 
   const float* means = a.means;
   const float* scales = reinterpret_cast<const float*>(a.scales);
   const float* quats = reinterpret_cast<const float*>(a.quats);
-  const float* opac = reinterpret_cast<const float*>(a.opac);
   const float* shs = reinterpret_cast<const float*>(a.sh);
   const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
   const float qr[4] = {quats[4 * i], quats[4 * i + 1], quats[4 * i + 2], quats[4 * i + 3]};
   const float sx = scales[3 * i], sy = scales[3 * i + 1], sz = scales[3 * i + 2];
-  const float o = opac[i];
   const int ncoef = (a.sh_degree + 1) * (a.sh_degree + 1);
 
   const float qn = rsqrtf(qr[0] * qr[0] + qr[1] * qr[1] + qr[2] * qr[2] + qr[3] * qr[3]);
@@ -549,8 +549,6 @@ __global__ void __launch_bounds__(128) k_project_backward(PanelGeom g, CamTable 
   out.opacities[i] = gr.grad_opac[i];
   for (int c = 0; c < ncoef; ++c)
     for (int u = 0; u < 3; ++u) out.sh[((size_t)i * ncoef + c) * 3 + u] = dsh[c][u];
-  (void)o;
-  (void)kLn2;
 }
 
 }  // namespace
