@@ -79,7 +79,7 @@ struct lfd_batch {
   Buf proj_means[kMaxBatchScenes], proj_co[kMaxBatchScenes], proj_ct[kMaxBatchScenes],
       proj_depth[kMaxBatchScenes];
   // global scratch
-  Buf item_key[2], item_val[2], counts_nat, counts, offsets, scan_tmp, bin_desc;
+  Buf item_key[2], item_val[2], emit_pos, counts, offsets, scan_tmp, bin_desc;
   Buf pair_key[2], pair_val[2], radix_tmp, ranges, small, work;
 };
 
@@ -105,7 +105,7 @@ void lfd_batch_destroy(lfd_batch* b) {
     b->proj_ct[s].release();
     b->proj_depth[s].release();
   }
-  Buf* all[] = {&b->item_key[0], &b->item_key[1], &b->item_val[0], &b->item_val[1], &b->counts_nat,
+  Buf* all[] = {&b->item_key[0], &b->item_key[1], &b->item_val[0], &b->item_val[1], &b->emit_pos,
                 &b->counts, &b->offsets, &b->scan_tmp, &b->bin_desc, &b->pair_key[0],
                 &b->pair_key[1], &b->pair_val[0], &b->pair_val[1], &b->radix_tmp, &b->ranges,
                 &b->small, &b->work};
@@ -201,7 +201,7 @@ int lfd_batch_reserve(lfd_batch* b, const int64_t* max_gaussians, int64_t max_pa
     B_CUDA(b->pair_key[k].ensure((size_t)(max_pairs + 1) * 4));
     B_CUDA(b->pair_val[k].ensure((size_t)(max_pairs + 1) * 4));
   }
-  B_CUDA(b->counts_nat.ensure(items4));
+  B_CUDA(b->emit_pos.ensure(items4));
   B_CUDA(b->counts.ensure(items4));
   B_CUDA(b->offsets.ensure(items4));
   B_CUDA(b->scan_tmp.ensure(scan_temp_bytes(items + 1)));
@@ -256,12 +256,12 @@ int lfd_batch_render(lfd_batch* b, const lfd_gaussians* scenes, const lfd_camera
     const int64_t M = scenes[s].count;
     const int64_t n = (int64_t)b->g[s].K * M;
     if (n == 0) continue;
+    // counts and descriptors written at each item's emission position
+    B_CUDA(launch_invert_u32(order + item_off[s], n, b->emit_pos.as<uint32_t>() + item_off[s], st));
     B_CUDA(launch_bin_count(b->g[s], M, b->proj_means[s].as<float>(), b->proj_co[s].as<float>(),
-                            b->proj_ct[s].as<float>(), nullptr, n,
-                            b->counts_nat.as<uint32_t>() + item_off[s],
+                            b->proj_ct[s].as<float>(), nullptr, b->emit_pos.as<uint32_t>() + item_off[s],
+                            n, b->counts.as<uint32_t>() + item_off[s],
                             desc + (size_t)item_off[s] * kBinDescBytes, st));
-    B_CUDA(launch_gather_u32(b->counts_nat.as<uint32_t>() + item_off[s], order + item_off[s], n,
-                             b->counts.as<uint32_t>() + item_off[s], st));
   }
   B_CUDA(scan_exclusive(b->counts.as<uint32_t>(), b->offsets.as<uint32_t>(), n_items, b->scan_tmp.p,
                         d_small, st));

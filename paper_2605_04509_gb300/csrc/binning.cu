@@ -248,8 +248,8 @@ constexpr int kBoxFields = 6;  // mx, my, bx0, bx1, y0, y1 (y0 > y1: not seen)
 __global__ void __launch_bounds__(32 * kBinWarps)
     k_bin_count(PanelGeom g, int64_t M, const float2* __restrict__ means2d,
                 const float4* __restrict__ conic_opacity, const float4* __restrict__ color_tau,
-                const uint32_t* __restrict__ order, int64_t n_items, uint32_t* __restrict__ counts,
-                BinDesc* __restrict__ desc) {
+                const uint32_t* __restrict__ order, const uint32_t* __restrict__ dest,
+                int64_t n_items, uint32_t* __restrict__ counts, BinDesc* __restrict__ desc) {
   __shared__ uint32_t s_n[kBinWarps][32];
   extern __shared__ float s_box[];  // [kBoxFields][C][32 * kBinWarps]
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -262,8 +262,11 @@ __global__ void __launch_bounds__(32 * kBinWarps)
   constexpr int kItems = 32 * kBinWarps;
   auto box = [&](int f, int l, int item) -> float& { return s_box[(f * g.C + l) * kItems + item]; };
   const int my_item = warp * 32 + lane;
+  // where the item's count and descriptor go: its emission position
+  int64_t o = s;
   if (in) {
     r = order ? order[s] : (uint32_t)s;
+    if (dest) o = dest[r];
     const float4 co = conic_opacity[r];
     ok = bin_prep(co.x, co.y, co.z, color_tau[r].w, q);
   }
@@ -298,7 +301,6 @@ __global__ void __launch_bounds__(32 * kBinWarps)
   int U;
   const int ubase = warp_exclusive(wide ? 0 : rows, lane, &U);
   __syncwarp();
-  const int64_t s_warp0 = s - lane;
   for (int b = 0; b < U; b += 32) {
     const int u = b + lane;
     const int j = unit_owner(ubase, u);
@@ -307,6 +309,7 @@ __global__ void __launch_bounds__(32 * kBinWarps)
     const int ty0j = __shfl_sync(0xffffffffu, ty0, j);
     const int c0j = __shfl_sync(0xffffffffu, c0, j);
     const bool fitsj = __shfl_sync(0xffffffffu, fits, j);
+    const int64_t oj = (int64_t)__shfl_sync(0xffffffffu, (unsigned long long)o, j);
     if (u < U) {
       const int item_j = warp * 32 + j;
       const int ty = ty0j + rr;
@@ -327,14 +330,14 @@ __global__ void __launch_bounds__(32 * kBinWarps)
         mask |= bits << (a - c0j);
       }
       atomicAdd(&s_n[warp][j], (uint32_t)__popcll(mask));
-      if (desc && fitsj) desc[s_warp0 + j].mask[rr] = mask;
+      if (desc && fitsj) desc[oj].mask[rr] = mask;
     }
   }
   __syncwarp();
   if (in) {
-    counts[s] = wide ? n_self : s_n[warp][lane];
+    counts[o] = wide ? n_self : s_n[warp][lane];
     if (desc)
-      desc[s].header = rows == 0 ? 0ull
+      desc[o].header = rows == 0 ? 0ull
                                  : ((unsigned long long)ty0 | ((unsigned long long)c0 << 16) |
                                     ((unsigned long long)rows << 32) |
                                     ((unsigned long long)(fits ? 0 : 1) << 40));
@@ -440,7 +443,7 @@ __global__ void __launch_bounds__(32 * kEmitWarps)
     r = order ? order[s] : (uint32_t)s;
     n = counts[s];
     pos = offsets[s];
-    if (n) h = desc[r].header;
+    if (n) h = desc[s].header;
   }
   const unsigned valid = __ballot_sync(0xffffffffu, in);
   if (!valid) return;
@@ -479,10 +482,9 @@ __global__ void __launch_bounds__(32 * kEmitWarps)
   for (int it = 0; it < 8; ++it) {
     const int j = it * 4 + (lane >> 3);
     const int part = lane & 7;  // 16-byte part: words 2 part, 2 part + 1
-    const uint32_t rj = __shfl_sync(0xffffffffu, r, j);
     const int uj = __shfl_sync(0xffffffffu, units, j);
     if (uj > 0 && 2 * part <= uj) {
-      const uint4 w = reinterpret_cast<const uint4*>(desc + rj)[part];
+      const uint4 w = reinterpret_cast<const uint4*>(desc + (s - lane + j))[part];
       reinterpret_cast<uint4*>(&s_desc[warp][j][0])[part] = w;
     }
   }
@@ -528,6 +530,11 @@ __global__ void k_gather_u32(const uint32_t* __restrict__ src, const uint32_t* _
                              int64_t n, uint32_t* __restrict__ dst) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s < n) dst[s] = src[idx[s]];
+}
+
+__global__ void k_invert_u32(const uint32_t* __restrict__ perm, int64_t n, uint32_t* __restrict__ inv) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) inv[perm[s]] = (uint32_t)s;
 }
 
 // One thread per (tile, cluster) run: lower bounds of its key and of the
@@ -610,8 +617,8 @@ cudaError_t launch_item_keys(const PanelGeom& g, int64_t M, const float* depth,
 
 cudaError_t launch_bin_count(const PanelGeom& g, int64_t M, const float* means2d,
                              const float* conic_opacity, const float* color_tau,
-                             const uint32_t* order, int64_t n_items, uint32_t* counts, void* desc,
-                             cudaStream_t s) {
+                             const uint32_t* order, const uint32_t* dest, int64_t n_items,
+                             uint32_t* counts, void* desc, cudaStream_t s) {
   if (n_items == 0) return cudaSuccess;
   const size_t smem = (size_t)kBoxFields * g.C * 32 * kBinWarps * sizeof(float);
   if (smem > 48 * 1024) {
@@ -622,7 +629,7 @@ cudaError_t launch_bin_count(const PanelGeom& g, int64_t M, const float* means2d
   k_bin_count<<<blocks_for(n_items, 32 * kBinWarps), 32 * kBinWarps, smem, s>>>(
       g, M, reinterpret_cast<const float2*>(means2d),
       reinterpret_cast<const float4*>(conic_opacity), reinterpret_cast<const float4*>(color_tau),
-      order, n_items, counts, reinterpret_cast<BinDesc*>(desc));
+      order, dest, n_items, counts, reinterpret_cast<BinDesc*>(desc));
   note_launches(1);
   return cudaGetLastError();
 }
@@ -670,6 +677,13 @@ cudaError_t launch_gather_u32(const uint32_t* src, const uint32_t* idx, int64_t 
                               cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   k_gather_u32<<<blocks_for(n, 256), 256, 0, s>>>(src, idx, n, dst);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_invert_u32(const uint32_t* perm, int64_t n, uint32_t* inv, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_invert_u32<<<blocks_for(n, 256), 256, 0, s>>>(perm, n, inv);
   note_launches(1);
   return cudaGetLastError();
 }

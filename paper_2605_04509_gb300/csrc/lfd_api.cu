@@ -113,7 +113,7 @@ struct lfd_plan {
   // per-frame scratch
   DevBuf proj_means, proj_co, proj_ct, proj_depth;
   DevBuf item_key[2], item_val[2];
-  DevBuf counts, counts_nat, offsets, scan_tmp, bin_desc;
+  DevBuf counts, emit_pos, offsets, scan_tmp, bin_desc;
   DevBuf pair_key[2], pair_val[2];
   DevBuf radix_tmp;
   DevBuf ranges;
@@ -251,7 +251,7 @@ void lfd_plan_destroy(lfd_plan* p) {
   cudaFree(p->seg);
   DevBuf* bufs[] = {&p->proj_means, &p->proj_co,   &p->proj_ct,     &p->proj_depth,
                     &p->item_key[0], &p->item_key[1], &p->item_val[0], &p->item_val[1],
-                    &p->counts,     &p->counts_nat, &p->offsets,   &p->scan_tmp,    &p->bin_desc,  &p->pair_key[0],
+                    &p->counts,     &p->emit_pos, &p->offsets,   &p->scan_tmp,    &p->bin_desc,  &p->pair_key[0],
                     &p->pair_key[1], &p->pair_val[0], &p->pair_val[1], &p->radix_tmp,
                     &p->ranges,     &p->small,     &p->host_in[0],  &p->host_in[1],
                     &p->host_in[2], &p->host_in[3], &p->host_in[4], &p->image,
@@ -547,7 +547,7 @@ static int render_projected_impl(lfd_plan* p, int64_t M, const float* means2d,
   // ---- stage 2: key generation ----
   if ((rc = p->counts.ensure((size_t)(n_items + 1) * 4)) != LFD_OK) return rc;
   if ((rc = p->offsets.ensure((size_t)(n_items + 1) * 4)) != LFD_OK) return rc;
-  if ((rc = p->counts_nat.ensure((size_t)(n_items + 1) * 4)) != LFD_OK) return rc;
+  if ((rc = p->emit_pos.ensure((size_t)(n_items + 1) * 4)) != LFD_OK) return rc;
   if ((rc = p->scan_tmp.ensure(scan_temp_bytes(n_items + 1))) != LFD_OK) return rc;
   if ((rc = p->bin_desc.ensure((size_t)(n_items + 1) * kBinDescBytes)) != LFD_OK) return rc;
   const uint32_t* order = nullptr;
@@ -566,14 +566,17 @@ static int render_projected_impl(lfd_plan* p, int64_t M, const float* means2d,
                             nullptr, 0, 32 + g.bit_k, p->radix_tmp.p, &alt, d_err, s));
     order = p->item_val[alt ? 1 : 0].as<uint32_t>();
   }
-  // tile counts and union descriptors in natural (cluster, Gaussian) order:
-  // coalesced attribute reads; the counts are then gathered into the
-  // emission order for the offsets scan
-  LFD_CUDA(launch_bin_count(g, M, means2d, conic_opacity, color_tau, nullptr, n_items,
-                            order ? p->counts_nat.as<uint32_t>() : p->counts.as<uint32_t>(),
-                            p->bin_desc.p, s));
-  if (order)
-    LFD_CUDA(launch_gather_u32(p->counts_nat.as<uint32_t>(), order, n_items, p->counts.as<uint32_t>(), s));
+  // tile counts and union descriptors: the count pass reads the items in
+  // natural (cluster, Gaussian) order (coalesced attribute reads) and writes
+  // each item's count and descriptor at its emission position, so that the
+  // offsets scan and the emit pass read them in order
+  uint32_t* emit_pos = nullptr;
+  if (order) {
+    emit_pos = p->emit_pos.as<uint32_t>();
+    LFD_CUDA(launch_invert_u32(order, n_items, emit_pos, s));
+  }
+  LFD_CUDA(launch_bin_count(g, M, means2d, conic_opacity, color_tau, nullptr, emit_pos, n_items,
+                            p->counts.as<uint32_t>(), p->bin_desc.p, s));
   LFD_CUDA(scan_exclusive(p->counts.as<uint32_t>(), p->offsets.as<uint32_t>(), n_items, p->scan_tmp.p,
                           d_small, s));
   unsigned long long P = (unsigned long long)p->cap_P;
@@ -926,7 +929,7 @@ int lfd_plan_reserve(lfd_plan* p, int64_t max_gaussians, int64_t max_pairs) {
       (rc = p->proj_co.ensure((size_t)(n + 1) * 16)) != LFD_OK ||
       (rc = p->proj_ct.ensure((size_t)(n + 1) * 16)) != LFD_OK ||
       (rc = p->proj_depth.ensure(items4)) != LFD_OK || (rc = p->counts.ensure(items4)) != LFD_OK ||
-      (rc = p->offsets.ensure(items4)) != LFD_OK || (rc = p->counts_nat.ensure(items4)) != LFD_OK ||
+      (rc = p->offsets.ensure(items4)) != LFD_OK || (rc = p->emit_pos.ensure(items4)) != LFD_OK ||
       (rc = p->scan_tmp.ensure(scan_temp_bytes(n + 1))) != LFD_OK ||
       (rc = p->bin_desc.ensure((size_t)(n + 1) * kBinDescBytes)) != LFD_OK ||
       (rc = p->radix_tmp.ensure(sort_tmp)) != LFD_OK ||

@@ -69,20 +69,23 @@ cudaError_t launch_item_keys(const PanelGeom& g, int64_t M, const float* depth,
 // Bytes per item of the optional union descriptors the count pass leaves for
 // the emit pass (nullptr: the emit pass recomputes the geometry).
 constexpr size_t kBinDescBytes = 128;
-// tile count of the cluster union per item; items given by `order` (flat
-// k*M + i indices) or natural order when order == nullptr
+// tile count of the cluster union per item; items visited in `order` (flat
+// k*M + i indices) or natural order when order == nullptr. The count and the
+// descriptor of item r go to position dest[r] (its emission position), or to
+// the visit position when dest == nullptr.
 cudaError_t launch_bin_count(const PanelGeom& g, int64_t M, const float* means2d,
                              const float* conic_opacity, const float* color_tau,
-                             const uint32_t* order, int64_t n_items, uint32_t* counts, void* desc,
-                             cudaStream_t s);
+                             const uint32_t* order, const uint32_t* dest, int64_t n_items,
+                             uint32_t* counts, void* desc, cudaStream_t s);
 // emission: key32 = (t << bit_k) | k when keys64 == nullptr, else Eq. 11
 cudaError_t launch_bin_emit(const PanelGeom& g, int64_t M, const float* means2d,
                             const float* conic_opacity, const float* color_tau,
                             const float* depth, const uint32_t* order, int64_t n_items,
                             const uint32_t* offsets, uint32_t* keys32, uint64_t* keys64,
                             uint32_t* vals, const void* desc, cudaStream_t s);
-// emission from descriptors indexed by item r (written by a natural-order
-// count pass); items visited in `order`, counts/offsets indexed by position
+// emission from descriptors written by the count pass at each item's
+// emission position; items visited in `order`, counts/offsets/descriptors
+// indexed by position
 // Writes nothing when *P_dev > P_cap (P_dev non-null); then sets bit 1 of
 // *err (capacity overflow).
 cudaError_t launch_bin_emit_coop(const PanelGeom& g, int64_t M, const float* means2d,
@@ -95,6 +98,8 @@ cudaError_t launch_bin_emit_coop(const PanelGeom& g, int64_t M, const float* mea
 // dst[s] = src[idx[s]]
 cudaError_t launch_gather_u32(const uint32_t* src, const uint32_t* idx, int64_t n, uint32_t* dst,
                               cudaStream_t s);
+// inv[perm[s]] = s
+cudaError_t launch_invert_u32(const uint32_t* perm, int64_t n, uint32_t* inv, cudaStream_t s);
 // [S_tk, E_tk) of every (tile, cluster) run by binary search in the sorted
 // keys (empty runs get (0, 0)); P a capacity, the live count from *P_dev
 // when non-null. Writes the whole table.

@@ -127,7 +127,7 @@ extern "C" int lfd_render_projected_noalloc(lfd_plan* plan, int64_t M, const flo
                            0, 32 + g.bit_k, temp, &alt, d_err, s));
     order = item_val[alt ? 1 : 0];
   }
-  NA_CUDA(launch_bin_count(g, M, means2d, conic_opacity, color_tau, order, n_items, counts,
+  NA_CUDA(launch_bin_count(g, M, means2d, conic_opacity, color_tau, order, nullptr, n_items, counts,
                            nullptr, s));
   NA_CUDA(scan_exclusive(counts, offsets, n_items, temp, d_small, s));
   NA_CUDA(cudaMemcpyAsync(pv.h_small, d_small, 4 * sizeof(unsigned long long),
