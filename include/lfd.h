@@ -247,14 +247,33 @@ LFD_API int lfd_render_fullframe(lfd_plan *plan, const lfd_gaussians *g, const l
  * and out_rgb are host pointers (pinned memory gives the fastest copies). The
  * call copies the inputs to plan-owned device memory, renders, copies the
  * image back and returns once it is in out_rgb (or, on an error, once every
- * copy it queued has finished). The copies run on a plan-owned transfer
- * stream: the Gaussians go up in four chunks, each projected as it lands,
- * and the remapped blend runs in four bands of tile rows on plan-owned
- * streams forked from `stream`, each band's rows copied back as soon as the
- * band is done. The image equals lfd_render's bit for bit. */
+ * copy it queued has finished). The copies run on plan-owned upload and
+ * download streams: the Gaussians go up in four chunks, each projected as it
+ * lands, and the remapped blend runs in four bands of tile rows on
+ * plan-owned streams forked from `stream`, each band's rows copied back as
+ * soon as the band is done. The image equals lfd_render's bit for bit. It is
+ * lfd_render_host_async followed by lfd_render_host_wait. */
 LFD_API int lfd_render_host(lfd_plan *plan, const lfd_gaussians *g_host,
                     const lfd_camera *cams, int32_t num_cams, float *out_rgb_host,
                     void *stream, lfd_stats *stats);
+
+/* Pipelined form of lfd_render_host for a stream of frames (same arguments):
+ * queues the frame and returns once its pair count has been read back (the
+ * frame's one mid-frame synchronisation), while its blend and the copy of
+ * its image to out_rgb_host may still be running; the next call's upload then
+ * runs under this frame's blend. The plan keeps two sets of device input and
+ * image buffers and alternates them frame by frame. The host Gaussian arrays
+ * and out_rgb_host of every queued frame must stay valid, the inputs
+ * unchanged and out_rgb_host unread, until lfd_render_host_wait returns.
+ * Frames of one plan go on one stream. On an error it waits for the copies
+ * it queued before returning. */
+LFD_API int lfd_render_host_async(lfd_plan *plan, const lfd_gaussians *g_host,
+                                  const lfd_camera *cams, int32_t num_cams, float *out_rgb_host,
+                                  void *stream, lfd_stats *stats);
+
+/* Wait until every frame queued with lfd_render_host_async on this plan has
+ * its image in host memory. LFD_ERR_CUDA if a copy failed. */
+LFD_API int lfd_render_host_wait(lfd_plan *plan);
 
 /* Copy the last frame's sorted Gaussian list L (uint32 [P], Gaussian ids),
  * range table (uint32 [T][K][2] = [S, E), (0, 0) when empty) and, with

@@ -82,12 +82,15 @@ bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 }  // namespace
 
 namespace {
-// Transfers of lfd_render_host, overlapped with the frame's kernels: the
-// Gaussians go up in kHostChunks chunks on a transfer stream and each chunk
-// is projected as soon as it has landed; the remapped blend runs in
-// kHostBands bands of tile rows, launched on streams of their own so that
-// each band's last blocks share the GPU with the next band's first ones, and
-// each band's image rows go back as soon as the band is done.
+// Transfers of lfd_render_host(_async), overlapped with the kernels: the
+// Gaussians go up in kHostChunks chunks on an upload stream and each chunk is
+// projected as soon as it has landed; the remapped blend runs in kHostBands
+// bands of tile rows, launched on streams of their own so that each band's
+// last blocks share the GPU with the next band's first ones, and each band's
+// image rows go back on a download stream as soon as the band is done. The
+// device copies of the inputs and the device image are double-buffered
+// (parity of the frame), so a frame's upload can run under the previous
+// frame's blend.
 constexpr int kHostChunks = 4;
 constexpr int kHostBands = 4;
 struct HostIO {
@@ -95,6 +98,17 @@ struct HostIO {
   void* dst[5];         // their device copies
   size_t elem_bytes[5];  // bytes per Gaussian of each array
   float* out_host;      // host image [H][W][3]
+  int parity;           // which of the double buffers the frame uses
+};
+struct HostPipe {
+  cudaStream_t up = nullptr, down = nullptr;  // upload, download
+  cudaStream_t band[kHostBands] = {};
+  cudaEvent_t chunk[kHostChunks] = {};
+  cudaEvent_t band_done[kHostBands] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t inputs_free[2] = {};  // the projection that read input buffer f ended
+  cudaEvent_t image_free[2] = {};   // the download of device image f ended
+  int frame = 0;                    // frames queued so far
 };
 }  // namespace
 
@@ -118,14 +132,12 @@ struct lfd_plan {
   DevBuf radix_tmp;
   DevBuf ranges;
   DevBuf small;  // [0] total pairs, [1], [2] evaluation counters, [3] wait-error bits
-  DevBuf host_in[5];  // device copies of host Gaussians (lfd_render_host)
-  DevBuf image;       // device image for lfd_render_host
+  DevBuf host_in[2][5];  // device copies of host Gaussians (lfd_render_host), double-buffered
+  DevBuf image[2];       // device images for lfd_render_host
   DevBuf g_means2d, g_conic, g_color, g_opac;  // backward scratch
   DevBuf keep;  // LFD_FLAG_KEEP_BLEND_STATE: [T][cap] stop index, final T
-  // lfd_render_host: transfer stream and its events (created on first use)
-  cudaStream_t io_stream = nullptr;
-  cudaStream_t band_stream[kHostBands] = {};
-  cudaEvent_t io_ev[2 + kHostChunks + kHostBands] = {};
+  HostPipe io;  // lfd_render_host streams and events (created on first use)
+  bool io_ready = false;
   unsigned long long* h_small = nullptr;  // pinned
   // last frame
   int64_t last_P = -1;
@@ -253,19 +265,32 @@ void lfd_plan_destroy(lfd_plan* p) {
                     &p->item_key[0], &p->item_key[1], &p->item_val[0], &p->item_val[1],
                     &p->counts,     &p->emit_pos, &p->offsets,   &p->scan_tmp,    &p->bin_desc,  &p->pair_key[0],
                     &p->pair_key[1], &p->pair_val[0], &p->pair_val[1], &p->radix_tmp,
-                    &p->ranges,     &p->small,     &p->host_in[0],  &p->host_in[1],
-                    &p->host_in[2], &p->host_in[3], &p->host_in[4], &p->image,
+                    &p->ranges,     &p->small,     &p->host_in[0][0], &p->host_in[0][1],
+                    &p->host_in[0][2], &p->host_in[0][3], &p->host_in[0][4], &p->host_in[1][0],
+                    &p->host_in[1][1], &p->host_in[1][2], &p->host_in[1][3], &p->host_in[1][4],
+                    &p->image[0],   &p->image[1],
                     &p->g_means2d,  &p->g_conic,   &p->g_color,     &p->g_opac, &p->keep};
   for (DevBuf* b : bufs) b->release();
   if (p->h_small) cudaFreeHost(p->h_small);
   for (auto& set : p->ev)
     for (cudaEvent_t& e : set)
       if (e) cudaEventDestroy(e);
-  for (cudaEvent_t& e : p->io_ev)
+  HostPipe& io = p->io;
+  if (io.up) cudaStreamSynchronize(io.up);
+  if (io.down) cudaStreamSynchronize(io.down);
+  for (cudaEvent_t e : io.chunk)
     if (e) cudaEventDestroy(e);
-  if (p->io_stream) cudaStreamDestroy(p->io_stream);
-  for (cudaStream_t& b : p->band_stream)
+  for (cudaEvent_t e : io.band_done)
+    if (e) cudaEventDestroy(e);
+  for (int f = 0; f < 2; ++f) {
+    if (io.inputs_free[f]) cudaEventDestroy(io.inputs_free[f]);
+    if (io.image_free[f]) cudaEventDestroy(io.image_free[f]);
+  }
+  if (io.fork) cudaEventDestroy(io.fork);
+  for (cudaStream_t b : io.band)
     if (b) cudaStreamDestroy(b);
+  if (io.up) cudaStreamDestroy(io.up);
+  if (io.down) cudaStreamDestroy(io.down);
   delete p;
 }
 
@@ -483,9 +508,9 @@ static int project_impl(lfd_plan* p, const lfd_gaussians* gs, const lfd_camera* 
     if (!io) {
       e = launch_project(p->g, *t, a, s);
     } else {
-      // the transfer stream starts after the work already queued on s
-      e = cudaEventRecord(p->io_ev[0], s);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(p->io_stream, p->io_ev[0], 0);
+      // the upload overwrites input buffers the projection two frames ago read
+      HostPipe& hp = p->io;
+      e = cudaStreamWaitEvent(hp.up, hp.inputs_free[io->parity], 0);
       const int64_t M = gs->count;
       for (int c = 0; c < kHostChunks && e == cudaSuccess; ++c) {
         const int64_t m0 = M * c / kHostChunks, m1 = M * (c + 1) / kHostChunks;
@@ -493,13 +518,14 @@ static int project_impl(lfd_plan* p, const lfd_gaussians* gs, const lfd_camera* 
         for (int b = 0; b < 5 && e == cudaSuccess; ++b)
           e = cudaMemcpyAsync(static_cast<char*>(io->dst[b]) + m0 * io->elem_bytes[b],
                               static_cast<const char*>(io->src[b]) + m0 * io->elem_bytes[b],
-                              (size_t)(m1 - m0) * io->elem_bytes[b], cudaMemcpyHostToDevice, p->io_stream);
-        if (e == cudaSuccess) e = cudaEventRecord(p->io_ev[1 + c], p->io_stream);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->io_ev[1 + c], 0);
+                              (size_t)(m1 - m0) * io->elem_bytes[b], cudaMemcpyHostToDevice, hp.up);
+        if (e == cudaSuccess) e = cudaEventRecord(hp.chunk[c], hp.up);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, hp.chunk[c], 0);
         a.m_begin = m0;
         a.m_end = m1;
         if (e == cudaSuccess) e = launch_project(p->g, *t, a, s);
       }
+      if (e == cudaSuccess) e = cudaEventRecord(hp.inputs_free[io->parity], s);
     }
     if (e != cudaSuccess) rc = fail_cuda(e, "project");
   }
@@ -647,18 +673,18 @@ static int render_projected_impl(lfd_plan* p, int64_t M, const float* means2d,
   const bool kept = (p->flags & LFD_FLAG_KEEP_BLEND_STATE) && p->opts.remap && !p->fullframe;
   ba.keep = kept ? p->keep.as<uint2>() : nullptr;
   const size_t row_floats = (size_t)g.W * 3;
-  if (p->fullframe) {
-    LFD_CUDA(launch_blend_fullframe(g, ba, s));
-  } else if (p->opts.remap && io) {
-    // bands of tile rows, forked from s and joined back into it
-    cudaEvent_t ev_fork = p->io_ev[1 + kHostChunks + kHostBands];
-    LFD_CUDA(cudaEventRecord(ev_fork, s));
+  if (p->opts.remap && !p->fullframe && io) {
+    // bands of tile rows, forked from s and joined back into it; the device
+    // image is written once the download of its previous frame has ended
+    HostPipe& hp = p->io;
+    LFD_CUDA(cudaStreamWaitEvent(s, hp.image_free[io->parity], 0));
+    LFD_CUDA(cudaEventRecord(hp.fork, s));
     int done = 0;
     for (int b = 0; b < kHostBands; ++b) {
       const int ty0 = done, ty1 = g.TY * (b + 1) / kHostBands;
-      cudaStream_t sb = p->band_stream[b];
-      cudaEvent_t ev_b = p->io_ev[1 + kHostChunks + b];
-      LFD_CUDA(cudaStreamWaitEvent(sb, ev_fork, 0));
+      cudaStream_t sb = hp.band[b];
+      cudaEvent_t ev_b = hp.band_done[b];
+      LFD_CUDA(cudaStreamWaitEvent(sb, hp.fork, 0));
       if (ty1 > ty0) {
         done = ty1;
         ba.t_begin = ty0 * g.TX;
@@ -669,25 +695,31 @@ static int render_projected_impl(lfd_plan* p, int64_t M, const float* means2d,
       LFD_CUDA(cudaStreamWaitEvent(s, ev_b, 0));
       if (ty1 > ty0) {
         const int y0 = ty0 * g.TH, y1 = min(ty1 * g.TH, g.H);
-        LFD_CUDA(cudaStreamWaitEvent(p->io_stream, ev_b, 0));
+        LFD_CUDA(cudaStreamWaitEvent(hp.down, ev_b, 0));
         LFD_CUDA(cudaMemcpyAsync(io->out_host + (size_t)y0 * row_floats, out_rgb + (size_t)y0 * row_floats,
                                  (size_t)(y1 - y0) * row_floats * sizeof(float), cudaMemcpyDeviceToHost,
-                                 p->io_stream));
+                                 hp.down));
       }
     }
+    LFD_CUDA(cudaEventRecord(hp.image_free[io->parity], hp.down));
     ba.t_begin = 0;
     ba.t_end = -1;
-  } else if (p->opts.remap) {
-    LFD_CUDA(launch_blend(g, ba, s));
   } else {
-    LFD_CUDA(launch_blend_raster(g, ba, s));
+    if (io) LFD_CUDA(cudaStreamWaitEvent(s, p->io.image_free[io->parity], 0));
+    if (p->fullframe)
+      LFD_CUDA(launch_blend_fullframe(g, ba, s));
+    else if (p->opts.remap)
+      LFD_CUDA(launch_blend(g, ba, s));
+    else
+      LFD_CUDA(launch_blend_raster(g, ba, s));
   }
   if (io && (p->fullframe || !p->opts.remap)) {
-    cudaEvent_t ev_b = p->io_ev[1 + kHostChunks];
-    LFD_CUDA(cudaEventRecord(ev_b, s));
-    LFD_CUDA(cudaStreamWaitEvent(p->io_stream, ev_b, 0));
+    HostPipe& hp = p->io;
+    LFD_CUDA(cudaEventRecord(hp.band_done[0], s));
+    LFD_CUDA(cudaStreamWaitEvent(hp.down, hp.band_done[0], 0));
     LFD_CUDA(cudaMemcpyAsync(io->out_host, out_rgb, (size_t)g.H * row_floats * sizeof(float),
-                             cudaMemcpyDeviceToHost, p->io_stream));
+                             cudaMemcpyDeviceToHost, hp.down));
+    LFD_CUDA(cudaEventRecord(hp.image_free[io->parity], hp.down));
   }
   if (timing) {
     LFD_CUDA(cudaEventRecord(ev[4], s));
@@ -860,52 +892,85 @@ int lfd_render_fullframe(lfd_plan* p, const lfd_gaussians* gs, const lfd_camera*
   return lfd_render(p->ff_child, gs, cams, num_cams, out_rgb, stream, stats);
 }
 
-int lfd_render_host(lfd_plan* p, const lfd_gaussians* gh, const lfd_camera* cams, int32_t num_cams,
-                    float* out_rgb_host, void* stream, lfd_stats* stats) {
+static int create_host_pipe(HostPipe& hp) {
+  for (cudaStream_t& b : hp.band)
+    if (!b) LFD_CUDA(cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking));
+  if (!hp.up) LFD_CUDA(cudaStreamCreateWithFlags(&hp.up, cudaStreamNonBlocking));
+  if (!hp.down) LFD_CUDA(cudaStreamCreateWithFlags(&hp.down, cudaStreamNonBlocking));
+  cudaEvent_t* evs[] = {&hp.chunk[0], &hp.chunk[1], &hp.chunk[2], &hp.chunk[3],
+                        &hp.band_done[0], &hp.band_done[1], &hp.band_done[2], &hp.band_done[3],
+                        &hp.fork, &hp.inputs_free[0], &hp.inputs_free[1], &hp.image_free[0],
+                        &hp.image_free[1]};
+  static_assert(kHostChunks == 4 && kHostBands == 4, "event list");
+  for (cudaEvent_t* e : evs)
+    if (!*e) LFD_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  return LFD_OK;
+}
+
+// let every copy the host pipe has queued finish (they read or write the
+// caller's host buffers)
+static cudaError_t drain_host_pipe(const HostPipe& hp) {
+  cudaError_t e1 = hp.up ? cudaStreamSynchronize(hp.up) : cudaSuccess;
+  cudaError_t e2 = hp.down ? cudaStreamSynchronize(hp.down) : cudaSuccess;
+  return e1 != cudaSuccess ? e1 : e2;
+}
+
+int lfd_render_host_async(lfd_plan* p, const lfd_gaussians* gh, const lfd_camera* cams,
+                          int32_t num_cams, float* out_rgb_host, void* stream, lfd_stats* stats) {
   if (!p) return fail(LFD_ERR_INVALID, "NULL plan");
   if (!out_rgb_host) return fail(LFD_ERR_INVALID, "out_rgb_host is NULL");
   if (!gh) return fail(LFD_ERR_INVALID, "gaussians is NULL");
   const int64_t M = gh->count;
   if (M < 0 || gh->sh_degree < 0 || gh->sh_degree > 3) return fail(LFD_ERR_INVALID, "bad Gaussian set");
+  int rc;
+  if (!p->io_ready) {
+    if ((rc = create_host_pipe(p->io)) != LFD_OK) return rc;
+    p->io_ready = true;
+  }
+  const int f = p->io.frame & 1;
   const int ncoef = (gh->sh_degree + 1) * (gh->sh_degree + 1);
   const size_t es = gh->attr_dtype == LFD_DTYPE_F32 ? 4 : 2;
   HostIO io;
+  io.parity = f;
   const size_t eb[5] = {12, 3 * es, 4 * es, es, (size_t)ncoef * 3 * es};
   const void* src[5] = {gh->means, gh->scales, gh->quats, gh->opacities, gh->sh};
-  int rc;
   for (int b = 0; b < 5; ++b) {
-    if ((rc = p->host_in[b].ensure((size_t)M * eb[b] + 16)) != LFD_OK) return rc;
     if (M > 0 && !src[b]) return fail(LFD_ERR_INVALID, "NULL Gaussian attribute");
+    if ((rc = p->host_in[f][b].ensure((size_t)M * eb[b] + 16)) != LFD_OK) return rc;
     io.src[b] = src[b];
-    io.dst[b] = p->host_in[b].p;
+    io.dst[b] = p->host_in[f][b].p;
     io.elem_bytes[b] = eb[b];
   }
   io.out_host = out_rgb_host;
   const size_t out_bytes = (size_t)p->g.W * p->g.H * 3 * sizeof(float);
-  if ((rc = p->image.ensure(out_bytes)) != LFD_OK) return rc;
-  if (!p->io_stream) {  // created last: set once everything else exists
-    for (cudaStream_t& b : p->band_stream)
-      if (!b) LFD_CUDA(cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking));
-    for (cudaEvent_t& e : p->io_ev)
-      if (!e) LFD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    LFD_CUDA(cudaStreamCreateWithFlags(&p->io_stream, cudaStreamNonBlocking));
-  }
+  if ((rc = p->image[f].ensure(out_bytes)) != LFD_OK) return rc;
   lfd_gaussians gd = *gh;
-  gd.means = p->host_in[0].as<float>();
-  gd.scales = p->host_in[1].p;
-  gd.quats = p->host_in[2].p;
-  gd.opacities = p->host_in[3].p;
-  gd.sh = p->host_in[4].p;
-  cudaStream_t s = (cudaStream_t)stream;
-  rc = render_impl(p, &gd, cams, num_cams, p->image.as<float>(), stream, stats, &io);
-  // copies already queued read or write the caller's host buffers: let them
-  // finish before returning, whatever the outcome
-  const cudaError_t e1 = cudaStreamSynchronize(p->io_stream);
-  const cudaError_t e2 = cudaStreamSynchronize(s);
-  if (rc != LFD_OK) return rc;
-  if (e1 != cudaSuccess) return fail_cuda(e1, "host transfers");
-  if (e2 != cudaSuccess) return fail_cuda(e2, "render");
+  gd.means = p->host_in[f][0].as<float>();
+  gd.scales = p->host_in[f][1].p;
+  gd.quats = p->host_in[f][2].p;
+  gd.opacities = p->host_in[f][3].p;
+  gd.sh = p->host_in[f][4].p;
+  rc = render_impl(p, &gd, cams, num_cams, p->image[f].as<float>(), stream, stats, &io);
+  ++p->io.frame;
+  if (rc != LFD_OK) {
+    drain_host_pipe(p->io);
+    return rc;
+  }
   return LFD_OK;
+}
+
+int lfd_render_host_wait(lfd_plan* p) {
+  if (!p) return fail(LFD_ERR_INVALID, "NULL plan");
+  const cudaError_t e = drain_host_pipe(p->io);
+  if (e != cudaSuccess) return fail_cuda(e, "host transfers");
+  return LFD_OK;
+}
+
+int lfd_render_host(lfd_plan* p, const lfd_gaussians* gh, const lfd_camera* cams, int32_t num_cams,
+                    float* out_rgb_host, void* stream, lfd_stats* stats) {
+  const int rc = lfd_render_host_async(p, gh, cams, num_cams, out_rgb_host, stream, stats);
+  if (rc != LFD_OK) return rc;
+  return lfd_render_host_wait(p);
 }
 
 int lfd_plan_reserve(lfd_plan* p, int64_t max_gaussians, int64_t max_pairs) {

@@ -108,6 +108,9 @@ def load() -> ct.CDLL:
                             ct.POINTER(CStats)], ct.c_int),
             "lfd_render_projected_noalloc": ([_P, ct.c_int64, _P, _P, _P, _P, _P, _P,
                                               ct.POINTER(CStats)], ct.c_int),
+            "lfd_render_host_async": ([_P, ct.POINTER(CGaussians), ct.POINTER(CCamera), ct.c_int32,
+                                       _P, _P, ct.POINTER(CStats)], ct.c_int),
+            "lfd_render_host_wait": ([_P], ct.c_int),
             "lfd_render_host": ([_P, ct.POINTER(CGaussians), ct.POINTER(CCamera), ct.c_int32,
                                  _P, _P, ct.POINTER(CStats)], ct.c_int),
             "lfd_render_backward": ([_P, ct.POINTER(CGaussians), ct.POINTER(CCamera), ct.c_int32,
@@ -214,6 +217,7 @@ class Plan:
         _check(L.lfd_plan_create(ct.byref(cp), ct.byref(co), ct.byref(h)))
         self._h = h
         self.flags = 0
+        self._pending = []  # host tensors of queued lfd_render_host_async frames
         self.tile = tuple(tile)
         self.views_per_cluster = views_per_cluster
         self.sort_mode = sort_mode
@@ -338,6 +342,24 @@ class Plan:
         _check(load().lfd_render_host(self._h, ct.byref(g), carr, n, out_host.data_ptr(),
                                       _stream_ptr(stream), ct.byref(st)))
         return out_host, st.as_dict()
+
+    def render_host_async(self, scene_host, cams: np.ndarray, out_host, stream=None):
+        """lfd_render_host_async: queue a frame; out_host is filled by the time
+        render_host_wait() returns. The host tensors are kept alive until then."""
+        g = gaussians_struct(scene_host, host=True)
+        carr, n = cameras_array(cams)
+        st = CStats()
+        self._pending.append((scene_host, out_host, carr))
+        _check(load().lfd_render_host_async(self._h, ct.byref(g), carr, n, out_host.data_ptr(),
+                                            _stream_ptr(stream), ct.byref(st)))
+        return out_host, st.as_dict()
+
+    def render_host_wait(self):
+        """lfd_render_host_wait: every queued frame's image is in host memory."""
+        try:
+            _check(load().lfd_render_host_wait(self._h))
+        finally:
+            self._pending = []
 
     def reserve(self, max_gaussians: int, max_pairs: int):
         """lfd_plan_reserve: capacity mode (no read-back; graph-capturable

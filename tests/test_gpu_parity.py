@@ -338,6 +338,31 @@ def test_host_entry_point_matches_device(tiny, remap):
     plan.close()
 
 
+def test_host_pipelined_frames_match_device(tiny):
+    # several frames queued with lfd_render_host_async before one wait: each
+    # frame's upload runs under the previous frame's blend and the plan
+    # alternates two sets of device buffers; one frame has fewer Gaussians
+    w, scene, cams = tiny
+    plan = lfd.Plan(w.panel, views_per_cluster=8)
+    scenes = [scene,
+              dict(scene, opacities=(scene["opacities"] * 0.5).astype(np.float32)),
+              {k: v[: len(v) // 2] for k, v in scene.items()},
+              dict(scene, means=(scene["means"] + 0.05).astype(np.float32))]
+    refs = [plan.render(lfd.scene_to_device(sc), cams)[0].cpu() for sc in scenes]
+    hosts = [{k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in sc.items()}
+             for sc in scenes]
+    outs = [torch.full(refs[0].shape, -1.0, dtype=torch.float32).pin_memory() for _ in scenes]
+    for _ in range(2):
+        for h, o in zip(hosts, outs):
+            plan.render_host_async(h, cams, o)
+        plan.render_host_wait()
+        for i, (o, r) in enumerate(zip(outs, refs)):
+            assert torch.equal(o, r), i
+        for o in outs:
+            o.fill_(-1.0)
+    plan.close()
+
+
 @pytest.mark.parametrize("height,count", [(32, 2001), (144, 3), (16, 0)])
 def test_host_entry_point_ragged(height, count):
     # fewer tile rows than bands, Gaussian counts not divisible by the chunk
