@@ -3,7 +3,7 @@ configuration): 16 seeded scenes (seeds 100-115) of 200k-3M Gaussians (log-
 uniform), panels assigned round-robin from 1536x2048 / 48 views,
 3840x2160 / 45 views and 7680x4320 / 100 views, all attributes in FP16.
 
-    python -m paper_2605_04509_gb300.batching [--frames 3] [--scenes 16]
+    python -m paper_2605_04509_gb300.batching [--frames 3] [--scenes 16] [--sizes 200000,3000000]
     python -m paper_2605_04509_gb300.batching --probe --tiles 16x16,32x16,32x16
 
 (--probe: only the batch, with the given tile per panel and no tuning or
@@ -62,12 +62,13 @@ def timed(fn, frames: int) -> float:
     return e0.elapsed_time(e1) / frames
 
 
-def run(frames: int = 3, n_scenes: int = 16, tune_frames: int = 2):
+def run(frames: int = 3, n_scenes: int = 16, tune_frames: int = 2, lo: int = 200_000,
+        hi: int = 3_000_000):
     import torch
 
     from . import autotune, lfd
 
-    sizes = scene_sizes(n_scenes)
+    sizes = scene_sizes(n_scenes, lo, hi)
     panel_of = [s % len(PANELS) for s in range(n_scenes)]
     t0 = time.perf_counter()
     scenes = [lfd.scene_to_device(synth.mixture_scene(sizes[s], 100 + s), attr_dtype=torch.float16)
@@ -179,7 +180,7 @@ def run(frames: int = 3, n_scenes: int = 16, tune_frames: int = 2):
 
     subpixels = sum(PANELS[panel_of[s]][1].subpixels for s in range(n_scenes))
     line = {
-        "workload": f"{n_scenes} scenes, 200k-3M Gaussians (log-uniform, seeds 100-{99 + n_scenes}), "
+        "workload": f"{n_scenes} scenes, {lo}-{hi} Gaussians (log-uniform, seeds 100-{99 + n_scenes}), "
                     "panels round-robin " + ", ".join(p[0] for p in PANELS) + ", FP16 attributes, "
                     "|V_k| = 8",
         "gaussians": sizes, "panels": [PANELS[p][0] for p in panel_of], "pairs": pairs,
@@ -228,12 +229,15 @@ def main():
     ap.add_argument("--scenes", type=int, default=16)
     ap.add_argument("--probe", action="store_true")
     ap.add_argument("--tiles", default="16x16,32x16,32x16")
+    ap.add_argument("--sizes", default="200000,3000000",
+                    help="lo,hi: Gaussian counts drawn log-uniform in [lo, hi]")
     args = ap.parse_args()
+    lo, hi = (int(v) for v in args.sizes.split(","))
     if args.probe:
         tiles = [tuple(int(v) for v in t.split("x")) for t in args.tiles.split(",")]
         probe(args.frames, args.scenes, tiles)
     else:
-        run(args.frames, args.scenes)
+        run(args.frames, args.scenes, lo=lo, hi=hi)
 
 
 if __name__ == "__main__":

@@ -254,26 +254,36 @@ __global__ void __launch_bounds__(256) k_blend(PanelGeom g, BlendArgs a) {
 }
 
 // Batched, persistent form: a grid sized to the GPU pulls (scene, cluster,
-// tile) runs from a work counter until all scenes' runs are done.
+// tile) runs from a work counter, kBatchChunk consecutive runs at a time (one
+// atomic and two barriers per chunk, not per run: most runs of a large panel
+// are short), until all scenes' runs are done.
+constexpr uint32_t kBatchChunk = 8;
+
+// (R <= 2: at most 48 registers, like the single-scene blend, so that eight
+// 160-thread blocks fit an SM rather than six)
 template <int R>
-__global__ void __launch_bounds__(256) k_blend_batch(BatchBlendArgs b) {
+__global__ void __launch_bounds__(256, R <= 2 ? 5 : 2) k_blend_batch(BatchBlendArgs b) {
   extern __shared__ float4 smem[];
   __shared__ uint32_t s_run;
   if (b.P_dev && *b.P_dev > b.P_cap) return;  // capacity overflow: leave the images
   for (;;) {
-    if (threadIdx.x == 0) s_run = atomicAdd(b.work, 1u);
+    if (threadIdx.x == 0) s_run = atomicAdd(b.work, kBatchChunk);
     __syncthreads();
-    const uint32_t r = s_run;
+    const uint32_t r0 = s_run;
     __syncthreads();
-    if (r >= b.total_runs) break;
+    if (r0 >= b.total_runs) break;
+    const uint32_t r1 = min(r0 + kBatchChunk, b.total_runs);
     int si = 0;
-    while (si + 1 < b.n_scenes && r >= b.sc[si + 1].run_base) ++si;
-    const SceneBlend& sc = b.sc[si];
-    const uint32_t local = r - sc.run_base;
-    const int k = (int)(local / (uint32_t)sc.g.T);
-    const int t = (int)(local - (uint32_t)k * (uint32_t)sc.g.T);
-    const uint2 rg = b.ranges[((size_t)si * b.T_max + t) * b.K_glob + k];
-    blend_run<R, false>(sc.g, sc.a, k, t, rg, smem);
+    for (uint32_t r = r0; r < r1; ++r) {
+      while (si + 1 < b.n_scenes && r >= b.sc[si + 1].run_base) ++si;
+      const SceneBlend& sc = b.sc[si];
+      const uint32_t local = r - sc.run_base;
+      const int k = (int)(local / (uint32_t)sc.g.T);
+      const int t = (int)(local - (uint32_t)k * (uint32_t)sc.g.T);
+      const uint2 rg = b.ranges[((size_t)si * b.T_max + t) * b.K_glob + k];
+      blend_run<R, false>(sc.g, sc.a, k, t, rg, smem);
+      __syncthreads();  // the next run restages shared memory
+    }
   }
 }
 
