@@ -82,11 +82,24 @@ __global__ void __launch_bounds__(128) k_project(PanelGeom g, CamTable cams, Pro
 
   const int ncoef = (a.sh_degree + 1) * (a.sh_degree + 1);
   float sh[16][3];
+  constexpr int kShVec = 48 * (int)sizeof(A) / 16;  // 16-byte loads of a degree-3 record
+  if (ncoef == 16 && (reinterpret_cast<uintptr_t>(shs) & 15) == 0) {
+    // degree 3: the record (48 values, a multiple of 16 bytes) in 16-byte loads
+    A raw[48];
+    const uint4* src = reinterpret_cast<const uint4*>(shs + (size_t)i * 48);
 #pragma unroll
-  for (int c = 0; c < 16; ++c) {
+    for (int v = 0; v < kShVec; ++v) reinterpret_cast<uint4*>(raw)[v] = src[v];
 #pragma unroll
-    for (int u = 0; u < 3; ++u)
-      sh[c][u] = c < ncoef ? to_f32(shs[((size_t)i * ncoef + c) * 3 + u]) : 0.f;
+    for (int c = 0; c < 16; ++c)
+#pragma unroll
+      for (int u = 0; u < 3; ++u) sh[c][u] = to_f32(raw[c * 3 + u]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+#pragma unroll
+      for (int u = 0; u < 3; ++u)
+        sh[c][u] = c < ncoef ? to_f32(shs[((size_t)i * ncoef + c) * 3 + u]) : 0.f;
+    }
   }
   const bool opaque_enough = (double)o >= 1.0 / 255.0;
   const float tau_i = 2.f * logf(255.f * o);
