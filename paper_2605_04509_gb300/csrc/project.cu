@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(128) k_project(PanelGeom g, CamTable cams, Pro
     a.depth[ok] = p.z;
     // Eq. 5: per-view 2D means of every slot of the cluster
     float2* mo = reinterpret_cast<float2*>(a.means2d) + ok * g.C;
-    for (int l = 0; l < g.C; ++l) {
+    auto mean_of = [&](int l) -> float2 {
       const int j = min(k * g.C + l, g.N - 1);
       const float* cj = cams.c[j];
       const float3 pj = cam_point(cj, mx, my, mz);
@@ -195,7 +195,16 @@ __global__ void __launch_bounds__(128) k_project(PanelGeom g, CamTable cams, Pro
         const float iz = 1.f / pj.z;
         m2 = make_float2(cj[12] * pj.x * iz + cj[14], cj[13] * pj.y * iz + cj[15]);
       }
-      mo[l] = m2;
+      return m2;
+    };
+    if ((g.C & 1) == 0 && (reinterpret_cast<uintptr_t>(mo) & 15) == 0) {
+      // two views per 16-byte store
+      for (int l = 0; l < g.C; l += 2) {
+        const float2 m0 = mean_of(l), m1 = mean_of(l + 1);
+        reinterpret_cast<float4*>(mo)[l >> 1] = make_float4(m0.x, m0.y, m1.x, m1.y);
+      }
+    } else {
+      for (int l = 0; l < g.C; ++l) mo[l] = mean_of(l);
     }
   }
 }
