@@ -387,8 +387,16 @@ __global__ void __launch_bounds__(128) k_project_backward(PanelGeom g, CamTable 
 
   float dmu[3] = {0.f, 0.f, 0.f};
   float dS3[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-  float dsh[16][3];
-  for (int c = 0; c < 16; ++c) dsh[c][0] = dsh[c][1] = dsh[c][2] = 0.f;
+  // the SH record in registers (zero past the degree), loops over all 16
+  // coefficients fully unrolled, so that nothing is indexed at run time
+  float sh[16][3], dsh[16][3];
+#pragma unroll
+  for (int c = 0; c < 16; ++c)
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      sh[c][u] = c < ncoef ? shs[((size_t)i * ncoef + c) * 3 + u] : 0.f;
+      dsh[c][u] = 0.f;
+    }
 
   for (int k = 0; k < g.K; ++k) {
     const size_t rec = (size_t)k * a.M + i;
@@ -439,13 +447,16 @@ __global__ void __launch_bounds__(128) k_project_backward(PanelGeom g, CamTable 
                             -8.f * kC3c * x * z, kC3e * (xx - yy), 0.f};
       const float gc[3] = {gcol.x, gcol.y, gcol.z};
       float ddx = 0.f, ddy = 0.f, ddz = 0.f;
+#pragma unroll
       for (int u = 0; u < 3; ++u) {
         float v = 0.5f;
-        for (int c = 0; c < ncoef; ++c) v += b[c] * shs[((size_t)i * ncoef + c) * 3 + u];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v += b[c] * sh[c][u];
         if (!(v > 0.f)) continue;  // clamped at zero: no gradient
-        for (int c = 0; c < ncoef; ++c) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
           dsh[c][u] += b[c] * gc[u];
-          const float sv = shs[((size_t)i * ncoef + c) * 3 + u] * gc[u];
+          const float sv = sh[c][u] * gc[u];
           ddx += bx[c] * sv;
           ddy += by[c] * sv;
           ddz += bz[c] * sv;
@@ -547,8 +558,11 @@ __global__ void __launch_bounds__(128) k_project_backward(PanelGeom g, CamTable 
     out.scales[3 * i + c] = ds[c];
   }
   out.opacities[i] = gr.grad_opac[i];
-  for (int c = 0; c < ncoef; ++c)
-    for (int u = 0; u < 3; ++u) out.sh[((size_t)i * ncoef + c) * 3 + u] = dsh[c][u];
+#pragma unroll
+  for (int c = 0; c < 16; ++c)
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+      if (c < ncoef) out.sh[((size_t)i * ncoef + c) * 3 + u] = dsh[c][u];
 }
 
 }  // namespace
