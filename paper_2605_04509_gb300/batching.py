@@ -49,6 +49,22 @@ def scene_sizes(n: int, lo: int = 200_000, hi: int = 3_000_000):
     return out
 
 
+def group_scenes(pairs, max_pairs: int = MAX_PAIRS, max_scenes: int = 16):
+    """Scenes (in order) grouped into as few batches as the pair limit and the
+    per-batch scene limit allow; a scene above the limit alone still gets a
+    batch of its own (its render then reports the capacity error)."""
+    groups, cur, cur_p = [], [], 0
+    for s, p in enumerate(pairs):
+        if cur and (cur_p + p > max_pairs or len(cur) == max_scenes):
+            groups.append(cur)
+            cur, cur_p = [], 0
+        cur.append(s)
+        cur_p += p
+    if cur:
+        groups.append(cur)
+    return groups
+
+
 def timed(fn, frames: int) -> float:
     import torch
     torch.cuda.synchronize()
@@ -111,14 +127,7 @@ def run(frames: int = 3, n_scenes: int = 16, tune_frames: int = 2, lo: int = 200
     ms_seq = timed(sequential, frames)
 
     # group scenes into batches below the pair limit (in scene order)
-    groups, cur, cur_p = [], [], 0
-    for s in range(n_scenes):
-        if cur and (cur_p + pairs[s] > MAX_PAIRS or len(cur) == 16):
-            groups.append(cur)
-            cur, cur_p = [], 0
-        cur.append(s)
-        cur_p += pairs[s]
-    groups.append(cur)
+    groups = group_scenes(pairs)
 
     def build(spt):
         pl = make_plans(spt)
