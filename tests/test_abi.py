@@ -49,6 +49,13 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert not h.value
     assert lib.lfd_plan_get_info(None, None) == lfd.LFD_ERR_INVALID
     assert lib.lfd_render(None, None, None, 0, None, None, None) == lfd.LFD_ERR_INVALID
+    assert lib.lfd_render_host(None, None, None, 0, None, None, None) == lfd.LFD_ERR_INVALID
+    assert lib.lfd_render_host_async(None, None, None, 0, None, None, None) == lfd.LFD_ERR_INVALID
+    assert lib.lfd_render_host_wait(None) == lfd.LFD_ERR_INVALID
+    assert lib.lfd_render_backward(None, None, None, 0, None, None, None, None, None, None,
+                                   None) == lfd.LFD_ERR_INVALID
+    assert lib.lfd_measure_alu_peaks(None, None, None) == lfd.LFD_ERR_INVALID
+    assert lib.lfd_set_flags(None, 0) == lfd.LFD_ERR_INVALID
     p = lfd.CPanel(100, 100, 300, 0.1, 4.0, 0.0)
     o = lfd.COpts(16, 16, 8, 1, 0, (ctypes.c_float * 3)())
     assert lib.lfd_plan_create(ctypes.byref(p), ctypes.byref(o), ctypes.byref(h)) == lfd.LFD_ERR_INVALID
