@@ -161,6 +161,21 @@ typedef struct {
   float ms_project, ms_keygen, ms_sort, ms_blend; /* stage times (flag)    */
 } lfd_stats;
 
+/* The display's view cone as cameras (Sec. 4 problem statement: the views
+ * of the 3D display setup; Alg. 1 inputs). Writes n (1..255) pinhole cameras
+ * to the host array out[n]: camera j on a horizontal arc of the given radius
+ * around the world origin at angle theta_j = -cone/2 + cone * j / (n - 1)
+ * (0 for n = 1), position (radius sin theta, 0, -radius cos theta), looking
+ * at the origin (z axis towards it, y axis the world's y, pointing down,
+ * x = y cross z: view 0 is the leftmost camera); R holds the x, y, z axes as
+ * rows and t = -R * position. fx = fy = (width / 2) / tan(fov_x / 2), principal
+ * point (width / 2, height / 2): every view renders at panel size. Angles in
+ * degrees; computed in double, stored as float. Host only (no device work).
+ * LFD_ERR_INVALID for n outside [1, 255], radius <= 0, fov_x outside (0, 180),
+ * cone outside [0, 360), width or height <= 0, or out == NULL. */
+LFD_API int lfd_make_arc_cameras(int32_t n, double cone_deg, double radius, double fov_x_deg,
+                                 int32_t width, int32_t height, lfd_camera *out);
+
 /* Create a plan for one panel and option set on the current device: builds
  * the view index matrix V (Eq. 1-3, FP64 arithmetic), the per-tile
  * view-sorted subpixel table Psi (Sec. 4.3, Eq. 8; "precomputed once since
@@ -285,11 +300,11 @@ LFD_API int lfd_plan_copy_lists(const lfd_plan *plan, uint32_t *list, uint32_t *
                         uint64_t *keys, int64_t capacity);
 
 /* Allocation-free variant of lfd_render_projected, for callers that must
- * not allocate device memory while they render: code that runs while a
- * stream is being captured into a CUDA graph (allocation calls cannot be
- * captured), real-time loops that cannot afford the device-wide
- * synchronisation cudaMalloc and cudaFree imply, and hosts whose own memory
- * manager owns the device heap. The paper has no counterpart.
+ * not allocate device memory while they render: real-time loops that cannot
+ * afford the device-wide synchronisation cudaMalloc and cudaFree imply, and
+ * hosts (plug-in and embedding environments) whose own memory manager owns
+ * the device heap. The paper has no counterpart. Callers that replay frames
+ * from a CUDA graph use capacity mode (lfd_plan_reserve) instead.
  * Same arguments, stages and results (bit for bit) as lfd_render_projected;
  * the plan must have been created beforehand. All scratch memory comes from
  * one fixed array of about 4.4 MB inside the library (every GPU that loads
@@ -303,7 +318,12 @@ LFD_API int lfd_plan_copy_lists(const lfd_plan *plan, uint32_t *list, uint32_t *
  * the array's device address once (set-up); make that first call before any
  * stream capture. Every call shares the one array and leaves its contents
  * behind, so calls that overlap on the GPU (other streams, other host
- * threads) race: serialise them. stats may be NULL; only num_pairs is filled. */
+ * threads) race: serialise them. stats may be NULL; only num_pairs is filled.
+ * A bounded wait of the sorts that gives up (LFD_ERR_TIMEOUT) is reported by
+ * this call when it happens before the pair-count read-back; one in the pair
+ * sort after it is reported by this call when stats is non-NULL (the call
+ * then synchronises the stream once more before returning), else by the next
+ * call. */
 LFD_API int lfd_render_projected_noalloc(lfd_plan *plan, int64_t M, const float *means2d,
                                          const float *conic_opacity, const float *color_tau,
                                          const float *depth, float *out_rgb, void *stream,

@@ -229,6 +229,50 @@ extern "C" {
 
 int lfd_version(void) { return 100; }
 
+// View-cone cameras (the "view cone" input of the problem statement and of
+// Alg. 1): n pinhole cameras on a horizontal arc of the given radius around
+// the world origin, all looking at it. Camera j sits at angle
+// theta_j = -cone/2 + cone * j / (n - 1) (0 when n = 1) at
+// (radius sin theta, 0, -radius cos theta); its axes are z towards the
+// origin, y the world's y (down) made orthogonal, x = y cross z (so view 0,
+// the leftmost camera, sees the scene from the left); R holds x, y, z as rows,
+// t = -R c. fx = fy = (W / 2) / tan(fov_x / 2), (cx, cy) = (W / 2, H / 2).
+// Computed in double precision, stored as float.
+int lfd_make_arc_cameras(int32_t n, double cone_deg, double radius, double fov_x_deg,
+                         int32_t width, int32_t height, lfd_camera* out) {
+  if (!out) return lfd::set_error(LFD_ERR_INVALID, "lfd_make_arc_cameras: out is NULL");
+  if (n < 1 || n > lfd::kMaxViews)
+    return lfd::set_error(LFD_ERR_INVALID, "lfd_make_arc_cameras: n must be in [1, 255]");
+  if (!(radius > 0.0) || !(fov_x_deg > 0.0 && fov_x_deg < 180.0) || !(cone_deg >= 0.0 && cone_deg < 360.0) ||
+      width <= 0 || height <= 0)
+    return lfd::set_error(LFD_ERR_INVALID,
+                          "lfd_make_arc_cameras: radius > 0, 0 < fov < 180, 0 <= cone < 360, W, H > 0");
+  const double kPi = 3.14159265358979323846;
+  const double f = (width / 2.0) / tan(fov_x_deg * kPi / 180.0 / 2.0);
+  for (int j = 0; j < n; ++j) {
+    const double th = n == 1 ? 0.0 : (-cone_deg / 2.0 + cone_deg * j / (n - 1)) * kPi / 180.0;
+    const double c[3] = {radius * sin(th), 0.0, -radius * cos(th)};
+    const double cn = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    const double z[3] = {-c[0] / cn, -c[1] / cn, -c[2] / cn};
+    const double y0[3] = {0.0, 1.0, 0.0};
+    double x[3] = {y0[1] * z[2] - y0[2] * z[1], y0[2] * z[0] - y0[0] * z[2], y0[0] * z[1] - y0[1] * z[0]};
+    const double xn = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+    for (int i = 0; i < 3; ++i) x[i] /= xn;
+    const double y[3] = {z[1] * x[2] - z[2] * x[1], z[2] * x[0] - z[0] * x[2], z[0] * x[1] - z[1] * x[0]};
+    const double* rows[3] = {x, y, z};
+    lfd_camera cam;
+    for (int r = 0; r < 3; ++r) {
+      for (int i = 0; i < 3; ++i) cam.R[3 * r + i] = (float)rows[r][i];
+      cam.t[r] = (float)(-(rows[r][0] * c[0] + rows[r][1] * c[1] + rows[r][2] * c[2]));
+    }
+    cam.fx = cam.fy = (float)f;
+    cam.cx = (float)(width / 2.0);
+    cam.cy = (float)(height / 2.0);
+    out[j] = cam;
+  }
+  return LFD_OK;
+}
+
 const char* lfd_status_string(int status) {
   switch (status) {
     case LFD_OK:

@@ -129,6 +129,8 @@ def load() -> ct.CDLL:
             "lfd_selftest_wait_timeout": ([_P], ct.c_int),
             "lfd_measure_alu_peaks": ([ct.POINTER(ct.c_double), ct.POINTER(ct.c_double), _P], ct.c_int),
             "lfd_kernel_launches": ([], ct.c_uint64),
+            "lfd_make_arc_cameras": ([ct.c_int32, ct.c_double, ct.c_double, ct.c_double, ct.c_int32,
+                                      ct.c_int32, ct.POINTER(CCamera)], ct.c_int),
             "lfd_status_string": ([ct.c_int], ct.c_char_p),
             "lfd_last_error": ([], ct.c_char_p),
             "lfd_version": ([], ct.c_int),
@@ -399,6 +401,17 @@ def measure_alu_peaks(stream=None) -> Dict[str, float]:
     f, e = ct.c_double(), ct.c_double()
     _check(load().lfd_measure_alu_peaks(ct.byref(f), ct.byref(e), _stream_ptr(stream)))
     return {"fp32_ops_per_s": f.value, "ex2_per_s": e.value}
+
+
+def make_arc_cameras(num_views: int, cone_deg: float, radius: float, fov_x_deg: float,
+                     width: int, height: int) -> np.ndarray:
+    """lfd_make_arc_cameras: the display's view cone as num_views pinhole
+    cameras; float32 [num_views, 16] rows (R[9], t[3], fx, fy, cx, cy)."""
+    arr = (CCamera * num_views)()
+    _check(load().lfd_make_arc_cameras(int(num_views), float(cone_deg), float(radius), float(fov_x_deg),
+                                       int(width), int(height), arr))
+    return np.ctypeslib.as_array(ct.cast(arr, ct.POINTER(ct.c_float)),
+                                 shape=(num_views, 16)).copy()
 
 
 def kernel_launches() -> int:
