@@ -2,11 +2,10 @@
 // stages of lfd_render_projected for small frames, with every piece of
 // scratch memory taken from one fixed array in device memory instead of
 // cudaMalloc. For callers that must not allocate device memory while they
-// render: code that runs while a CUDA stream is being captured into a graph
-// (allocation calls are not capturable), real-time loops whose latency budget
-// forbids the synchronisation that cudaMalloc/cudaFree imply, and hosts
-// whose memory manager owns the whole device heap. The paper has no
-// counterpart; the results equal lfd_render_projected's bit for bit.
+// render: real-time loops whose latency budget forbids the synchronisation
+// that cudaMalloc/cudaFree imply, and hosts whose memory manager owns the
+// whole device heap. The paper has no counterpart; the results equal
+// lfd_render_projected's bit for bit.
 #include <mutex>
 
 #include "lfd_internal.h"
@@ -178,6 +177,7 @@ extern "C" int lfd_render_projected_noalloc(lfd_plan* plan, int64_t M, const flo
   ba.eval_counter = nullptr;
   ba.max_segment = pv.max_segment;
   ba.V = pv.V;
+  ba.subpixels_per_thread = pv.subpixels_per_thread;
   if (pv.remap)
     NA_CUDA(launch_blend(g, ba, s));
   else
@@ -187,6 +187,16 @@ extern "C" int lfd_render_projected_noalloc(lfd_plan* plan, int64_t M, const flo
     stats->num_visits = -1;
     stats->num_evals = -1;
     stats->ms_project = stats->ms_keygen = stats->ms_sort = stats->ms_blend = -1.f;
+    // the caller asked for the frame's statistics: report a bounded wait of
+    // this call's pair sort now rather than at the next call
+    NA_CUDA(cudaMemcpyAsync(pv.h_small + 3, d_err, sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, s));
+    NA_CUDA(cudaStreamSynchronize(s));
+    if (pv.h_small[3] & 0xffffffffull) {
+      pv.h_small[3] = 0;
+      NA_CUDA(cudaMemsetAsync(d_err, 0, sizeof(unsigned long long), s));
+      return na_fail(LFD_ERR_TIMEOUT, "a bounded device wait of the pair sort gave up");
+    }
   }
   return LFD_OK;
 }

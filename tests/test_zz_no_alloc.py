@@ -1,11 +1,11 @@
 """lfd_render_projected_noalloc against lfd_render_projected.
 
 The allocation-free entry point serves callers that must not allocate device
-memory while they render (for example code running under CUDA stream capture,
-where cudaMalloc cannot be recorded, or a real-time loop that cannot afford
-the synchronisation an allocation implies). Its scratch lives in one fixed
-device array inside the library, so it handles small frames only. This file
-runs last so that a failure here does not hide any other test's result.
+memory while they render (a real-time loop that cannot afford the
+synchronisation an allocation implies, or a host whose own memory manager owns
+the device heap). Its scratch lives in one fixed device array inside the
+library, so it handles small frames only. This file runs last so that a
+failure here does not hide any other test's result.
 """
 import numpy as np
 import pytest
@@ -21,13 +21,15 @@ if not torch.cuda.is_available():  # pragma: no cover - CPU-only containers
 from paper_2605_04509_gb300 import lfd  # noqa: E402
 
 
-@pytest.mark.parametrize("c,sort_mode", [(8, lfd.SORT_DEPTH_FIRST), (1, lfd.SORT_DEPTH_FIRST),
-                                         (4, lfd.SORT_KEY64)])
-def test_noalloc_matches_allocating_entry_point(c, sort_mode):
+@pytest.mark.parametrize("c,sort_mode,spt", [(8, lfd.SORT_DEPTH_FIRST, 0), (1, lfd.SORT_DEPTH_FIRST, 0),
+                                             (4, lfd.SORT_KEY64, 0), (8, lfd.SORT_DEPTH_FIRST, 2)])
+def test_noalloc_matches_allocating_entry_point(c, sort_mode, spt):
     w = synth.WORKLOADS["tiny"]
     scene = synth.scene_for(w)
     cams = synth.arc_cameras(w.rig, w.panel.width, w.panel.height)
-    plan = lfd.Plan(w.panel, views_per_cluster=c, sort_mode=sort_mode, bg=(0.05, 0.1, 0.2))
+    # spt: the plan's subpixels-per-thread option reaches the blend of both calls
+    plan = lfd.Plan(w.panel, views_per_cluster=c, sort_mode=sort_mode, bg=(0.05, 0.1, 0.2),
+                    subpixels_per_thread=spt)
     attrs = plan.project(lfd.scene_to_device(scene), cams)
     want, st = plan.render_projected(attrs)
     want = want.clone()
