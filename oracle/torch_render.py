@@ -55,10 +55,13 @@ def _depth_f32(cam: np.ndarray, means32: np.ndarray) -> np.ndarray:
     return (d.astype(np.float32) + c[11]).astype(np.float32)
 
 
-def render(params: dict, cams: np.ndarray, V: np.ndarray, c: int, bg=(0.0, 0.0, 0.0)):
+def render(params: dict, cams: np.ndarray, V: np.ndarray, c: int, bg=(0.0, 0.0, 0.0),
+           alpha_min: float = ALPHA_MIN):
     """params: float64 tensors means [M,3], scales [M,3], quats [M,4] (w,x,y,z),
     opacities [M], sh [M,16,3] (requires_grad as needed). cams float32 [N,16].
-    V uint8 [H,W,3]. Returns the image [H,W,3] (float64)."""
+    V uint8 [H,W,3]. Returns the image [H,W,3] (float64). alpha_min is the
+    skip threshold of Eq. 10 (1/255); the tests move it by +-0.1 % to bracket
+    the definition's jump there (the accuracy reading of the render)."""
     means, scales, quats = params["means"], params["scales"], params["quats"]
     opac, sh = params["opacities"], params["sh"]
     H, W, _ = V.shape
@@ -113,7 +116,7 @@ def render(params: dict, cams: np.ndarray, V: np.ndarray, c: int, bg=(0.0, 0.0, 
         d = means - cpos[None, :]
         d = d / torch.linalg.norm(d, dim=1, keepdim=True)
         col = torch.clamp(torch.einsum("mc,mcu->mu", _sh_basis(d), sh) + 0.5, min=0.0)
-        valid = (zkey > np.float32(NEAR)) & (det.detach().numpy() > 0) & (opac.detach().numpy() >= ALPHA_MIN)
+        valid = (zkey > np.float32(NEAR)) & (det.detach().numpy() > 0) & (opac.detach().numpy() >= alpha_min)
         idx = np.nonzero(valid)[0]
         idx = idx[np.lexsort((idx, zkey[idx].astype(np.float64)))]
         if len(idx) == 0:
@@ -131,7 +134,7 @@ def render(params: dict, cams: np.ndarray, V: np.ndarray, c: int, bg=(0.0, 0.0, 
             qf = ca[it] * dx * dx + 2 * cb[it] * dx * dy + cc[it] * dy * dy  # [H, W, G]
             power = -0.5 * qf
             v = opac[it] * torch.exp(power)
-            keep = (power <= 0) & (v >= ALPHA_MIN) & vvalid[j][it][None, None, :]
+            keep = (power <= 0) & (v >= alpha_min) & vvalid[j][it][None, None, :]
             alpha = torch.where(keep, torch.minimum(v, torch.full_like(v, ALPHA_MAX)), torch.zeros_like(v))
             one_minus = 1 - alpha
             T_after = torch.cumprod(one_minus, dim=-1)

@@ -34,6 +34,22 @@ def test_forward_equals_c_oracle(c):
     assert img.max() > 0.3
 
 
+@pytest.mark.parametrize("rel", [-1e-3, 1e-3, 0.5])
+def test_forward_with_moved_threshold_equals_c_oracle(rel):
+    # the skip threshold moved as the bracket of the accuracy reading does
+    # (and far, to see that it acts): same image as the C oracle's
+    panel, scene, cams, V, _ = small_case(c=2)
+    a = oracle.ALPHA_MIN * (1 + rel)
+    img = torch_render.render(to_params(scene, False), cams, V, 2, alpha_min=a).numpy()
+    proj = oracle.project(scene, cams, panel.width, panel.height, 2)
+    with oracle.alpha_min(a):
+        ref, _ = oracle.render(proj, V, 2, mode=0)
+    np.testing.assert_allclose(img, ref, rtol=1e-10, atol=1e-12)
+    if rel == 0.5:
+        base = torch_render.render(to_params(scene, False), cams, V, 2).numpy()
+        assert np.abs(base - img).max() > 1e-3
+
+
 def _loss(params, cams, V, c, target):
     img = torch_render.render(params, cams, V, c)
     return ((img - target) ** 2).sum()
