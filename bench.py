@@ -93,6 +93,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fullframe", action="store_true", help="skip the full-frame baseline")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the FP16, |V_k| = 1 and batched forms reported beside the main line")
     ap.add_argument("--cpu-crop", default="1024x512", help="WxH of the oracle's central crop")
     return ap.parse_args()
 
@@ -288,11 +290,197 @@ def run_reference(args):
         "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cores, "kind": "oracle",
                          "sample": "per step: FP64 projection of all 1M Gaussians + binned FP64 "
                                    "blend of one 64x64-pixel crop (12,288 subpixels); frames/s = "
-                                   "crop subpixels / panel subpixels / time"},
+                                   "crop subpixels / panel subpixels / time. The rate is dominated by "
+                                   "the full-scene projection amortised over one small crop; the "
+                                   "oracle's rate on a 1024x512 crop is the main line's cpu_baseline"},
         "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def random_crops(panel, n, size, seed):
+    """n seeded size x size crops: the two opposite corners of the panel and
+    n - 2 uniform positions."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    W, H = panel.width, panel.height
+    out = [(0, 0, size, size), (W - size, H - size, W, H)]
+    while len(out) < n:
+        x0 = int(rng.integers(0, W - size + 1))
+        y0 = int(rng.integers(0, H - size + 1))
+        out.append((x0, y0, x0 + size, y0 + size))
+    return out
+
+
+MAX_ERR, MAX_FRAC_OFF = 2e-3, 1e-3
+
+
+def accuracy_over_crops(got, proj, V, C, tile, crops, first_ref=None, bg=(0.0, 0.0, 0.0)):
+    """Accuracy of the GPU image `got` [H, W, 3] against the FP64 oracle on
+    the given crops, under the bar's reading at the 1/255 threshold (the
+    definition rendered with the threshold moved by -/+0.1 %: where it jumps
+    by more than 1e-3 the value must lie within the span +- 2e-3; elsewhere
+    max |err| <= 2e-3; everywhere at most 0.1 % of subpixels off by more
+    than 1/255) and under the literal max |err| <= 2e-3."""
+    import numpy as np
+
+    import oracle
+    n = 0
+    sse = 0.0
+    max_err = max_reg = 0.0
+    jumps = outside = off = 0
+    for i, cr in enumerate(crops):
+        if i == 0 and first_ref is not None:
+            ref = first_ref
+        else:
+            ref, _ = oracle.render(proj, V, C, crop=cr, mode=1, tile=tile, bg=bg)
+        with oracle.alpha_min(oracle.ALPHA_MIN * (1 - 1e-3)):
+            lo, _ = oracle.render(proj, V, C, crop=cr, mode=1, tile=tile, bg=bg)
+        with oracle.alpha_min(oracle.ALPHA_MIN * (1 + 1e-3)):
+            hi, _ = oracle.render(proj, V, C, crop=cr, mode=1, tile=tile, bg=bg)
+        g = np.clip(got[cr[1]:cr[3], cr[0]:cr[2]].astype(np.float64), 0, 1)
+        r, a, b = np.clip(ref, 0, 1), np.clip(lo, 0, 1), np.clip(hi, 0, 1)
+        low = np.minimum(np.minimum(r, a), b)
+        high = np.maximum(np.maximum(r, a), b)
+        jump = (high - low) > MAX_ERR / 2
+        err = np.abs(g - r)
+        n += err.size
+        sse += float((err ** 2).sum())
+        max_err = max(max_err, float(err.max()))
+        if (~jump).any():
+            max_reg = max(max_reg, float(err[~jump].max()))
+        jumps += int(jump.sum())
+        outside += int(((g < low - MAX_ERR) | (g > high + MAX_ERR)).sum())
+        off += int((err > 1 / 255).sum())
+    mse = sse / max(n, 1)
+    frac_off = off / max(n, 1)
+    return {"vs": "FP64 oracle", "crops": [list(c) for c in crops], "subpixels": n,
+            "max_err": max_err, "literal_max_err_ok": max_err <= MAX_ERR,
+            "max_err_outside_threshold_jumps": max_reg, "threshold_jump_subpixels": jumps,
+            "outside_bracket_subpixels": outside, "frac_off_1_255": frac_off,
+            "bar_ok": bool(max_reg <= MAX_ERR and outside == 0 and frac_off <= MAX_FRAC_OFF),
+            "psnr_db": (float("inf") if mse == 0 else 10 * math.log10(1 / mse)),
+            "reading": "bar_ok: where the definition with the 1/255 threshold moved by -/+0.1 % "
+                       "jumps by more than 1e-3 the value lies within that span +- 2e-3; elsewhere "
+                       "max |err| <= 2e-3; <= 0.1 % of subpixels off by > 1/255"}
+
+
+def timed_frames(fn, frames, stream):
+    import torch
+    for _ in range(2):
+        fn()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(frames):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / frames
+
+
+def other_forms(args, w, scene, cams, tile, plan, out, stream, world, device, oracle_ok):
+    """The NEXT-row forms beside the plain FP32 frame, in the same run: FP16
+    attributes, the plain subpixel path without attribute reuse (|V_k| = 1),
+    and a batch of four scenes with mixed panels in one lfd_batch_render.
+    Each with an accuracy figure on a crop (FP64 oracle) or, for the batch,
+    bit-equality with the scenes' single-scene frames."""
+    import numpy as np
+    import torch
+
+    from paper_2605_04509_gb300 import batching, lfd, synth
+    S = w.panel.subpixels
+    frames = max(3, min(args.steps, 10))
+    forms = {}
+    crop = central_crop(w.panel, 256, 256)
+
+    def oracle_acc(sc, c, img):
+        if not oracle_ok:
+            return None
+        import oracle
+        cams_o = synth.arc_cameras(w.rig, w.panel.width, w.panel.height)
+        proj = oracle.project(sc, cams_o, w.panel.width, w.panel.height, c)
+        V = oracle.view_index(w.panel)
+        return accuracy_over_crops(img.cpu().numpy(), proj, V, c, tile, [crop])
+
+    # FP16 attributes (scales, rotations, opacity, SH; means FP32)
+    s16 = lfd.scene_to_device(scene, device, attr_dtype=torch.float16)
+    out16 = torch.empty_like(out)  # `out` keeps the FP32 frame for the main accuracy figure
+    ms = max_over_ranks(timed_frames(lambda: plan.render(s16, cams, out16, stream), frames, stream),
+                        world, device)
+    deq = {k: (v if k == "means" else v.astype(np.float16).astype(np.float32)) for k, v in scene.items()}
+    forms["fp16"] = {"value": world * 1000.0 / ms, "unit": "frames/s", "ms_per_frame": ms,
+                     "subpixels_per_s": world * S * 1000.0 / ms, "frames": frames,
+                     "what": "scales, rotations, opacity and SH stored in FP16 (means FP32); FP32 "
+                             "conic inverse, blend and transmittance",
+                     "accuracy": oracle_acc(deq, plan.views_per_cluster, out16),
+                     "accuracy_vs": "FP64 oracle fed the dequantised FP16 attributes, central 256x256 crop"}
+    del s16, out16
+    # plain subpixel path without reuse (|V_k| = 1), same tiles
+    plan1 = lfd.Plan(w.panel, tile=tile, views_per_cluster=1)
+    d32 = lfd.scene_to_device(scene, device)
+    out1 = torch.empty_like(out)
+    ms = max_over_ranks(timed_frames(lambda: plan1.render(d32, cams, out1, stream), max(3, frames // 2),
+                                     stream), world, device)
+    forms["c1_plain"] = {"value": world * 1000.0 / ms, "unit": "frames/s", "ms_per_frame": ms,
+                         "subpixels_per_s": world * S * 1000.0 / ms,
+                         "what": "|V_k| = 1: every view projected with its own covariance, depth and "
+                                 "colour (no attribute reuse), remapped blend",
+                         "accuracy": oracle_acc(scene, 1, out1),
+                         "accuracy_vs": "FP64 oracle (|V_k| = 1), central 256x256 crop"}
+    plan1.close()
+    del out1, d32
+    # a batch of four scenes with mixed panels, FP16 attributes, one
+    # lfd_batch_render (one persistent blend launch) per frame
+    n_sc = 4
+    sizes = batching.scene_sizes(n_sc)
+    panel_of = [sidx % len(batching.PANELS) for sidx in range(n_sc)]
+    tiles = {0: (16, 16), 1: (32, 16), 2: (32, 16)}
+    plans = {pi: lfd.Plan(batching.PANELS[pi][1], tile=tiles[pi], views_per_cluster=8)
+             for pi in set(panel_of)}
+    bcams = {pi: lfd.make_arc_cameras(r.num_views, r.cone_deg, r.radius, r.fov_x_deg, pn.width, pn.height)
+             for pi, (_nm, pn, r) in enumerate(batching.PANELS) if pi in plans}
+    bscenes = [lfd.scene_to_device(synth.mixture_scene(sizes[sidx], 100 + sidx), device,
+                                   attr_dtype=torch.float16) for sidx in range(n_sc)]
+    refs, pairs = [], []
+    for sidx in range(n_sc):
+        img, st = plans[panel_of[sidx]].render(bscenes[sidx], bcams[panel_of[sidx]])
+        refs.append(img.clone())
+        pairs.append(int(st["num_pairs"]))
+    souts = [torch.empty_like(r) for r in refs]
+
+    def seq():
+        for sidx in range(n_sc):
+            plans[panel_of[sidx]].render(bscenes[sidx], bcams[panel_of[sidx]], souts[sidx], stream)
+
+    ms_seq = max_over_ranks(timed_frames(seq, 3, stream), world, device)
+    batch = lfd.Batch([plans[panel_of[sidx]] for sidx in range(n_sc)])
+    batch.reserve(sizes, sum(pairs) + 1024)
+    bouts = batch.images()
+    ms_b = max_over_ranks(timed_frames(lambda: batch.render(bscenes, [bcams[pi] for pi in panel_of], bouts,
+                                                            stream), 3, stream), world, device)
+    batch.status()
+    same = all(torch.equal(o, r) for o, r in zip(bouts, refs))
+    sub = sum(batching.PANELS[pi][1].subpixels for pi in panel_of)
+    forms["batched"] = {"value": world * n_sc * 1000.0 / ms_b, "unit": "scenes/s", "ms_per_batch": ms_b,
+                        "subpixels_per_s": world * sub * 1000.0 / ms_b,
+                        "scenes": n_sc, "gaussians": sizes,
+                        "panels": [batching.PANELS[pi][0] for pi in panel_of],
+                        "tiles": [f"{tiles[pi][0]}x{tiles[pi][1]}" for pi in panel_of],
+                        "in_turn": {"value": world * n_sc * 1000.0 / ms_seq, "unit": "scenes/s",
+                                    "ms_per_round": ms_seq,
+                                    "what": "the same scenes as single-scene lfd_render frames"},
+                        "accuracy": {"images_identical_to_single_scene_frames": bool(same)},
+                        "what": "four scenes (log-uniform 200k-3M Gaussians, seeds 100-103), panels "
+                                "round-robin 1536x2048/48, 3840x2160/45, 7680x4320/100, FP16 attributes, "
+                                "one lfd_batch_render per round (reduced from the 16-scene batching "
+                                "workload to bound the bench's run time)"}
+    batch.close()
+    for pl in plans.values():
+        pl.close()
+    return forms
 
 
 # ---------------------------------------------------------------------------
@@ -311,7 +499,11 @@ def run_ours(args):
     w = synth.WORKLOADS[args.workload]
     C = args.views_per_cluster
     scene = synth.scene_for(w, args.gaussians or None)
-    cams = synth.arc_cameras(w.rig, w.panel.width, w.panel.height)
+    # the view cone through the library's own helper (lfd_make_arc_cameras);
+    # the oracle below takes the input generator's cameras (equal to float
+    # rounding, tested)
+    cams = lfd.make_arc_cameras(w.rig.num_views, w.rig.cone_deg, w.rig.radius, w.rig.fov_x_deg,
+                                w.panel.width, w.panel.height)
     dscene = lfd.scene_to_device(scene, device)
     autotune = None
     if args.tile == "auto":
@@ -475,37 +667,27 @@ def run_ours(args):
                        "synchronous": {"value": world * n_e2e / t_sync, "unit": "frames/s",
                                        "api": "lfd_render_host per frame (returns with the image)"}}
 
+    if not args.no_forms:
+        line["forms"] = other_forms(args, w, scene, cams, tile, plan, out, stream, world, device,
+                                    oracle_ok=(rank == 0 and world == 1 and not args.no_cpu_baseline))
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         cw, ch = (int(v) for v in args.cpu_crop.split("x"))
         crop = central_crop(w.panel, cw, ch)
-        ref, dt, sub = oracle_frame_sample(scene, cams, w.panel, C, tile, crop)
+        cams_o = synth.arc_cameras(w.rig, w.panel.width, w.panel.height)
+        ref, dt, sub = oracle_frame_sample(scene, cams_o, w.panel, C, tile, crop)
         cpu_fps = (sub / S) / dt
         line["cpu_baseline"] = {
             "value": cpu_fps, "unit": "frames/s", "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"FP64 projection of all {w.num_gaussians} Gaussians + binned FP64 blend of "
                       f"the central {cw}x{ch}-pixel crop ({sub} subpixels, {sub / S:.2%} of the "
                       f"frame) in {dt:.1f} s; frames/s = crop fraction / time"}
-        got = out.cpu().numpy()[crop[1]:crop[3], crop[0]:crop[2]].astype(np.float64)
-        # the definition with the 1/255 skip threshold moved by -/+0.1 %: where it
-        # jumps by more than 1e-3 a single Gaussian's ~1/255 contribution flips
-        proj = oracle.project(scene, cams, w.panel.width, w.panel.height, C)
+        got = out.cpu().numpy()
+        proj = oracle.project(scene, cams_o, w.panel.width, w.panel.height, C)
         V = oracle.view_index(w.panel)
-        with oracle.alpha_min(oracle.ALPHA_MIN * (1 - 1e-3)):
-            lo, _ = oracle.render(proj, V, C, crop=crop, mode=1, tile=tile)
-        with oracle.alpha_min(oracle.ALPHA_MIN * (1 + 1e-3)):
-            hi, _ = oracle.render(proj, V, C, crop=crop, mode=1, tile=tile)
-        g, r = np.clip(got, 0, 1), np.clip(ref, 0, 1)
-        lo, hi = np.clip(lo, 0, 1), np.clip(hi, 0, 1)
-        jump = (np.maximum(np.maximum(r, lo), hi) - np.minimum(np.minimum(r, lo), hi)) > 1e-3
-        err = np.abs(g - r)
-        mse = float((err ** 2).mean())
-        line["accuracy"] = {"vs": "FP64 oracle on the cpu_baseline crop",
-                            "max_err": float(err.max()),
-                            "max_err_outside_threshold_jumps": float(err[~jump].max()),
-                            "threshold_jump_subpixels": int(jump.sum()),
-                            "frac_off_1_255": float((err > 1 / 255).mean()),
-                            "psnr_db": (float("inf") if mse == 0 else 10 * math.log10(1 / mse))}
+        crops = [crop] + random_crops(w.panel, 8, 128, seed=12)
+        line["accuracy"] = accuracy_over_crops(got, proj, V, C, tile, crops, first_ref=ref)
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()

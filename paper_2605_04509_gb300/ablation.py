@@ -3,10 +3,13 @@ stage breakdown of T5/T6): cross-view attribute reuse on/off (clusters of 8
 views vs 1) and view-coherent remapping on/off, on one synthetic workload.
 
     python -m paper_2605_04509_gb300.ablation [--workload paper4k] [--frames 20] [--tile 32x16]
+    python -m paper_2605_04509_gb300.ablation --reuse [--workload paper4k]
 
 Prints one JSON line per configuration and a markdown table. Every
 configuration renders through the C ABI; the images of the remap on/off pairs
-are checked to be identical.
+are checked to be identical. --reuse reports the image-quality side of
+attribute reuse (Table 1's trend): PSNR of the |V_k| = 2, 4, 8, 16 renders
+against the exact |V_k| = 1 render of the same scene, over the whole panel.
 """
 from __future__ import annotations
 
@@ -68,14 +71,56 @@ def run(workload: str = "paper4k", frames: int = 20, warmup: int = 3, tile=(32, 
     return rows
 
 
+def reuse_quality(workload: str = "paper4k", sizes=(2, 4, 8, 16), tile=(32, 16)):
+    """PSNR, max |err| and share of subpixels off by more than 1/255 of the
+    |V_k| = c renders against the |V_k| = 1 render (clamped to [0, 1])."""
+    import math
+
+    import torch
+
+    from . import lfd, synth
+
+    w = synth.WORKLOADS[workload]
+    scene = synth.scene_for(w)
+    cams = synth.arc_cameras(w.rig, w.panel.width, w.panel.height)
+    s = lfd.scene_to_device(scene)
+    imgs = {}
+    for c in (1,) + tuple(sizes):
+        plan = lfd.Plan(w.panel, tile=tuple(tile), views_per_cluster=c)
+        out = torch.empty((w.panel.height, w.panel.width, 3), dtype=torch.float32, device="cuda")
+        plan.render(s, cams, out)
+        torch.cuda.synchronize()
+        imgs[c] = out.clamp(0, 1)
+        plan.close()
+    rows = []
+    for c in sizes:
+        err = (imgs[c] - imgs[1]).abs()
+        mse = float((err.double() ** 2).mean())
+        row = {"views_per_cluster": c, "psnr_db_vs_c1": float("inf") if mse == 0 else 10 * math.log10(1 / mse),
+               "max_err_vs_c1": float(err.max()), "frac_off_1_255": float((err > 1 / 255).float().mean())}
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    print("\n| |V_k| | PSNR vs |V_k| = 1 | max err | off by > 1/255 |")
+    print("|---|---|---|---|")
+    for r in rows:
+        print(f"| {r['views_per_cluster']} | {r['psnr_db_vs_c1']:.2f} dB | {r['max_err_vs_c1']:.3f} | "
+              f"{r['frac_off_1_255']:.2%} |")
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--workload", default="paper4k")
     ap.add_argument("--frames", type=int, default=20)
     ap.add_argument("--tile", default="32x16")
+    ap.add_argument("--reuse", action="store_true", help="image quality of attribute reuse vs |V_k|")
     args = ap.parse_args()
     np.set_printoptions(precision=3)
-    run(args.workload, args.frames, tile=tuple(int(v) for v in args.tile.split("x")))
+    tile = tuple(int(v) for v in args.tile.split("x"))
+    if args.reuse:
+        reuse_quality(args.workload, tile=tile)
+    else:
+        run(args.workload, args.frames, tile=tile)
 
 
 if __name__ == "__main__":

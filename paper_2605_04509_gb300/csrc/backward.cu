@@ -581,12 +581,14 @@ cudaError_t launch_blend_backward(const PanelGeom& g, const BlendArgs& a, const 
                       (a.keep ? 0 : (((size_t)g.C * block + 1) & ~(size_t)1) * sizeof(uint16_t) +
                                         (size_t)g.C * (nw + 1) * sizeof(int));
   const unsigned grid = (unsigned)((int64_t)g.K * g.T);
+  // the 48 KB default covers the kernel's static word as well
+  const bool big = smem + 16 > 48 * 1024;
   if (a.keep) {
-    if (smem > 48 * 1024)
+    if (big)
       cudaFuncSetAttribute(k_blend_backward<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_blend_backward<true><<<grid, block, smem, s>>>(g, a, gr);
   } else {
-    if (smem > 48 * 1024)
+    if (big)
       cudaFuncSetAttribute(k_blend_backward<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_blend_backward<false><<<grid, block, smem, s>>>(g, a, gr);
   }

@@ -621,7 +621,9 @@ cudaError_t launch_bin_count(const PanelGeom& g, int64_t M, const float* means2d
                              uint32_t* counts, void* desc, cudaStream_t s) {
   if (n_items == 0) return cudaSuccess;
   const size_t smem = (size_t)kBoxFields * g.C * 32 * kBinWarps * sizeof(float);
-  if (smem > 48 * 1024) {
+  // the 48 KB default covers static and dynamic shared memory together (the
+  // kernel's static part is its per-warp counters)
+  if (smem + sizeof(uint32_t) * 32 * kBinWarps > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;

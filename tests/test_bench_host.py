@@ -36,3 +36,48 @@ def test_blend_traffic_only_for_the_captured_source_and_tile():
     current = hashlib.sha256(open(src, "rb").read()).hexdigest() == fields["blend_cu_sha256"].strip()
     want = int(fields["dram_bytes_per_launch"].strip()) if current else None
     assert bench.blend_traffic_bytes(tile) == want
+
+
+def test_random_crops_in_bounds_with_both_corners():
+    from paper_2605_04509_gb300 import synth
+    panel = synth.WORKLOADS["paper4k"].panel
+    crops = bench.random_crops(panel, 8, 128, seed=12)
+    assert len(crops) == 8 and crops == bench.random_crops(panel, 8, 128, seed=12)
+    assert crops[0] == (0, 0, 128, 128)
+    assert crops[1] == (panel.width - 128, panel.height - 128, panel.width, panel.height)
+    for x0, y0, x1, y1 in crops:
+        assert 0 <= x0 and x1 <= panel.width and 0 <= y0 and y1 <= panel.height
+        assert x1 - x0 == 128 and y1 - y0 == 128
+
+
+def test_accuracy_verdicts_on_oracle_images():
+    # the oracle's own image passes both readings; a planted error of 3e-3
+    # away from any threshold jump fails both; a value inside a jump's span
+    # fails only the literal bar
+    import numpy as np
+
+    import oracle
+    from paper_2605_04509_gb300 import synth
+    w = synth.WORKLOADS["tiny"]
+    scene = synth.scene_for(w)
+    cams = synth.arc_cameras(w.rig, w.panel.width, w.panel.height)
+    proj = oracle.project(scene, cams, w.panel.width, w.panel.height, 4)
+    V = oracle.view_index(w.panel)
+    crops = [(0, 0, 256, 144)]
+    ref, lo, hi = oracle.render_bracket(proj, V, 4, mode=1)
+    a = bench.accuracy_over_crops(ref.copy(), proj, V, 4, (16, 16), crops)
+    assert a["bar_ok"] and a["literal_max_err_ok"] and a["max_err"] == 0.0
+    span = np.maximum(np.maximum(ref, lo), hi) - np.minimum(np.minimum(ref, lo), hi)
+    assert a["threshold_jump_subpixels"] == int((np.clip(span, 0, 1) > 1e-3).sum())
+    quiet = np.argwhere((span == 0) & (ref > 0.1) & (ref < 0.9))[0]
+    bad = ref.copy()
+    bad[tuple(quiet)] += 3e-3
+    b = bench.accuracy_over_crops(bad, proj, V, 4, (16, 16), crops)
+    assert not b["bar_ok"] and not b["literal_max_err_ok"]
+    jumps = np.argwhere((span > 3e-3) & (ref > 0.05) & (ref < 0.95))
+    if len(jumps):
+        j = tuple(jumps[0])
+        other = ref.copy()
+        other[j] = lo[j] if abs(lo[j] - ref[j]) > abs(hi[j] - ref[j]) else hi[j]
+        c = bench.accuracy_over_crops(other, proj, V, 4, (16, 16), crops)
+        assert c["bar_ok"] and not c["literal_max_err_ok"]
