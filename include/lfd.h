@@ -110,11 +110,10 @@ typedef struct {
  * [1, 32] (C = 1: no attribute reuse); remap 1 = view-coherent remapping
  * (Sec. 4.3), 0 = subpixels in raster order, each thread walking its own list
  * (the ablation "w/o remap"; same image); sort_mode one of LFD_SORT_*; bg is
- * the background colour added as T * bg. subpixels_per_thread (0 = automatic,
- * else 1, 2, 4 or 8) sets how many subpixels of a (tile, cluster) run one
- * blend thread owns, and with it the blend's staging depth (list entries
- * staged in shared memory per batch = threads per block); it changes speed
- * only, never the image. */
+ * the background colour added as T * bg. subpixels_per_thread (0, 1, 2, 4 or
+ * 8) is accepted and has no effect: the blend gives each (tile, cluster) run
+ * one warp, which stages 32 list entries per batch and takes the run's live
+ * subpixels 32 at a time. */
 typedef struct {
   int32_t tile_w, tile_h;
   int32_t views_per_cluster;

@@ -1,11 +1,12 @@
-"""Autotuner over the tile shape and the blend's staging depth.
+"""Autotuner over the tile shape.
 
 The tile shape changes how many Gaussian-(tile, cluster) pairs the key
 generation emits and sorts (smaller tiles: more pairs, shorter lists) and how
-many subpixels one blend block owns; subpixels_per_thread changes how many
-list entries the blend stages in shared memory per batch. Neither changes
-the image beyond the FP32 rounding of the tile-bin rule (the paper gives
-16x16 only as an example tile, Sec. 4.2). The tuner renders a few frames
+many subpixels one blend warp owns; it does not change the image beyond the
+FP32 rounding of the tile-bin rule (the paper gives 16x16 only as an example
+tile, Sec. 4.2). The plan's subpixels_per_thread option is still accepted as
+a candidate dimension, but the warp-per-run blend ignores it, so the default
+candidate list holds only 0. The tuner renders a few frames
 with each candidate plan on the caller's scene and cameras, times them with
 CUDA events on the rendering stream, checks every candidate's image against
 the first one's, and returns the fastest configuration.
@@ -21,7 +22,7 @@ import time
 from typing import Dict, Iterable, List, Optional, Tuple
 
 TILES: Tuple[Tuple[int, int], ...] = ((8, 8), (16, 8), (16, 16), (32, 8), (32, 16))
-SUBPIXELS_PER_THREAD: Tuple[int, ...] = (0, 1, 4)
+SUBPIXELS_PER_THREAD: Tuple[int, ...] = (0,)
 
 
 def time_plan(plan, scene, cams, out, frames: int, warmup: int) -> float:

@@ -9,9 +9,7 @@ uniform), panels assigned round-robin from 1536x2048 / 48 views,
 (--probe: only the batch, with the given tile per panel and no tuning or
 single-scene frames, rendered --frames times; for profiler launch lists.)
 
-Per panel the autotuner picks the tile shape on that panel's first scene;
-the staging depth (subpixels per blend thread) is then tuned for the whole
-batch. Scenes are grouped into as few batches as the 2^32 pair limit allows
+Per panel the autotuner picks the tile shape on that panel's first scene. Scenes are grouped into as few batches as the 2^32 pair limit allows
 (one for these sizes); each batch is one lfd_batch_render - one persistent
 blend launch - captured into a CUDA graph. It prints, as JSON lines, the
 tuning tables and the throughput of three schedules of the same work:
@@ -143,22 +141,7 @@ def run(frames: int = 3, n_scenes: int = 16, tune_frames: int = 2, lo: int = 200
         for b, g, outs in batches:
             b.render([scenes[s] for s in g], [cams[panel_of[s]] for s in g], outs)
 
-    # staging depth for the whole batch
-    depth_ms = {}
-    for spt in (0, 1, 4):
-        pl, batches = build(spt)
-        run_batches(batches)
-        for b, _, _ in batches:
-            b.status()
-        depth_ms[spt] = timed(lambda: run_batches(batches), tune_frames)
-        for b, _, _ in batches:
-            b.close()
-        for p in pl.values():
-            p.close()
-    spt = min(depth_ms, key=depth_ms.get)
-    print(json.dumps({"autotune_staging_depth": {str(k): round(v, 3) for k, v in depth_ms.items()},
-                      "chosen_subpixels_per_thread": spt}), flush=True)
-
+    spt = 0  # the warp-per-run blend has no staging-depth choice
     pl, batches = build(spt)
     run_batches(batches)
     total_pairs = 0

@@ -43,7 +43,12 @@ constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTMin = 1e-4f;
 
-constexpr int kNB = 32;  // list entries staged per batch: one per lane
+// list entries staged per batch: one per lane (more per lane cost more shared
+// memory per warp, and fewer resident warps, than they save)
+constexpr int kNE = 1;
+constexpr int kNB = 32 * kNE;
+typedef uint32_t ListBits;  // one list of a batch: bit e = entry e
+__device__ __forceinline__ int bits_first(ListBits b) { return __ffs(b) - 1; }
 
 // sub-tiles per tile for a cluster of C views: (view, sub-tile) bits fit 32
 __host__ __device__ inline int blend_subtiles(int C) { return C <= 16 ? 2 : 1; }
@@ -56,10 +61,10 @@ struct WarpSmem {
 __host__ __device__ inline WarpSmem warp_layout(int C, int S) {
   WarpSmem w;
   size_t o = 0;
-  w.co = o;   o += (size_t)kNB * 16;      // float4 [32]: scaled conic, skip threshold
-  w.oc = o;   o += (size_t)3 * kNB * 8;   // float2 [3][32]: (opacity, colour u)
-  w.mean = o; o += (size_t)C * kNB * 8;   // float2 [C][32]: per-view 2D means
-  w.mask = o; o += (size_t)kNB * 4;       // u32 [32]: entry bits (set-up: key histogram)
+  w.co = o;   o += (size_t)kNB * 16;      // float4 [kNB]: scaled conic, skip threshold
+  w.oc = o;   o += (size_t)3 * kNB * 8;   // float2 [3][kNB]: (opacity, colour u)
+  w.mean = o; o += (size_t)C * kNB * 8;   // float2 [C][kNB]: per-view 2D means
+  w.mask = o; o += (size_t)kNB * 4;       // u32 [kNB]: entry bits (set-up: key histogram)
   w.info = o; o += (size_t)S * 4;         // u32 [S]: packed subpixel (see pack_info)
   w.T = o;    o += (size_t)S * 4;         // float [S]: transmittance
   w.acc = o;  o += (size_t)S * 4;         // float [S]: colour so far
@@ -176,51 +181,56 @@ __device__ __forceinline__ void warp_blend_run(const PanelGeom& g, const BlendAr
   int n_live = n;
   unsigned long long n_visit = 0, n_eval = 0;
   for (uint32_t base = rg.x; base < rg.y && n_live > 0; base += kNB) {
-    // stage entry base + lane: attributes, per-view means, (view, sub-tile) bits
-    const uint32_t e = base + lane;
-    uint32_t mask = 0;
-    if (e < rg.y) {
-      const uint32_t gid = a.list[e];
-      const size_t rec = (size_t)k * a.M + gid;
-      const float4 co = reinterpret_cast<const float4*>(a.conic_opacity)[rec];
-      const float4 ct = reinterpret_cast<const float4*>(a.color_tau)[rec];
-      // w: log2 of the opacity ratio at which alpha reaches 1/255 (skip below)
-      s_co[lane] = make_float4(-0.5f * kLog2e * co.x, -kLog2e * co.y, -0.5f * kLog2e * co.z,
-                               -log2f(255.f * co.w) - 1e-4f);
-      s_oc[lane] = make_float2(co.w, ct.x);
-      s_oc[kNB + lane] = make_float2(co.w, ct.y);
-      s_oc[2 * kNB + lane] = make_float2(co.w, ct.z);
-      const float det = co.x * co.z - co.y * co.y;
-      const float hx = sqrtf(fmaxf(ct.w * co.z / det, 0.f));
-      const float hy = sqrtf(fmaxf(ct.w * co.x / det, 0.f));
-      // a view's box [mx -+ hx] x [my -+ hy] meets a sub-box iff its mean
-      // lies within these thresholds (hx, hy are shared by the cluster's
-      // views): x in [ax0, ax1] left half, [ax2, ax3] right half; y alike
-      const float ax0 = bx0 - hx, ax1 = bxl + hx, ax2 = bxr - hx, ax3 = bx1 + hx;
-      const float ay0 = by0 - hy, ay1 = byt + hy, ay2 = byb - hy, ay3 = by1 + hy;
-      const float2* mp = reinterpret_cast<const float2*>(a.means2d) + rec * C;
-      for (int l = 0; l < C; ++l) {
-        const float2 mu = mp[l];
-        s_mean[l * kNB + lane] = mu;
-        const bool xa = mu.x >= ax0 && mu.x <= ax1;
-        const bool xb = mu.x >= ax2 && mu.x <= ax3;
-        const bool ya = mu.y >= ay0 && mu.y <= ay1;
-        const bool yb = mu.y >= ay2 && mu.y <= ay3;
-        uint32_t bits;
-        if (Q == 1)
-          bits = (uint32_t)(xa && ya);
-        else if (Q == 2)
-          bits = (uint32_t)(xa && ya) | ((uint32_t)(xb && ya) << 1);
-        else
-          bits = (uint32_t)(xa && ya) | ((uint32_t)(xb && ya) << 1) | ((uint32_t)(xa && yb) << 2) |
-                 ((uint32_t)(xb && yb) << 3);
-        mask |= bits << (l * Q);
+    // stage entries base + j * 32 + lane: attributes, per-view means,
+    // (view, sub-tile) bits; then lane b holds list b of the batch
+    ListBits col = 0;
+#pragma unroll
+    for (int j = 0; j < kNE; ++j) {
+      const int slot_e = j * 32 + lane;
+      const uint32_t e = base + (uint32_t)slot_e;
+      uint32_t mask = 0;
+      if (e < rg.y) {
+        const uint32_t gid = a.list[e];
+        const size_t rec = (size_t)k * a.M + gid;
+        const float4 co = reinterpret_cast<const float4*>(a.conic_opacity)[rec];
+        const float4 ct = reinterpret_cast<const float4*>(a.color_tau)[rec];
+        // w: log2 of the opacity ratio at which alpha reaches 1/255 (skip below)
+        s_co[slot_e] = make_float4(-0.5f * kLog2e * co.x, -kLog2e * co.y, -0.5f * kLog2e * co.z,
+                                   -log2f(255.f * co.w) - 1e-4f);
+        s_oc[slot_e] = make_float2(co.w, ct.x);
+        s_oc[kNB + slot_e] = make_float2(co.w, ct.y);
+        s_oc[2 * kNB + slot_e] = make_float2(co.w, ct.z);
+        const float det = co.x * co.z - co.y * co.y;
+        const float hx = sqrtf(fmaxf(ct.w * co.z / det, 0.f));
+        const float hy = sqrtf(fmaxf(ct.w * co.x / det, 0.f));
+        // a view's box [mx -+ hx] x [my -+ hy] meets a sub-box iff its mean
+        // lies within these thresholds (hx, hy are shared by the cluster's
+        // views): x in [ax0, ax1] left half, [ax2, ax3] right half; y alike
+        const float ax0 = bx0 - hx, ax1 = bxl + hx, ax2 = bxr - hx, ax3 = bx1 + hx;
+        const float ay0 = by0 - hy, ay1 = byt + hy, ay2 = byb - hy, ay3 = by1 + hy;
+        const float2* mp = reinterpret_cast<const float2*>(a.means2d) + rec * C;
+        for (int l = 0; l < C; ++l) {
+          const float2 mu = mp[l];
+          s_mean[l * kNB + slot_e] = mu;
+          const bool xa = mu.x >= ax0 && mu.x <= ax1;
+          const bool xb = mu.x >= ax2 && mu.x <= ax3;
+          const bool ya = mu.y >= ay0 && mu.y <= ay1;
+          const bool yb = mu.y >= ay2 && mu.y <= ay3;
+          uint32_t bits;
+          if (Q == 1)
+            bits = (uint32_t)(xa && ya);
+          else if (Q == 2)
+            bits = (uint32_t)(xa && ya) | ((uint32_t)(xb && ya) << 1);
+          else
+            bits = (uint32_t)(xa && ya) | ((uint32_t)(xb && ya) << 1) | ((uint32_t)(xa && yb) << 2) |
+                   ((uint32_t)(xb && yb) << 3);
+          mask |= bits << (l * Q);
+        }
       }
+      if (COUNT) s_mask[slot_e] = mask;
+      const uint32_t cj = warp_bit_transpose(mask, lane);
+      col |= (ListBits)(lane < L ? cj : 0u) << (32 * j);
     }
-    if (COUNT) s_mask[lane] = mask;
-    // lane b: the batch's entries of list b
-    uint32_t col = warp_bit_transpose(mask, lane);
-    if (lane >= L) col = 0u;
     __syncwarp();
     const int nbatch = (int)min((uint32_t)kNB, rg.y - base);
     int w = 0;  // live subpixels kept so far (the live list is compacted in place)
@@ -233,29 +243,17 @@ __device__ __forceinline__ void warp_blend_run(const PanelGeom& g, const BlendAr
       const int xl = (int)((inf >> 13) & 63u), yl = (int)((inf >> 19) & 63u);
       const int slot = (int)(inf >> 25);
       const float px = (float)(x0 + xl) + 0.5f, py = (float)(y0 + yl) + 0.5f;
-      uint32_t bits = __shfl_sync(full, col, slot * Q + sub_of(xl, yl));
-      if (!has) bits = 0u;
+      ListBits bits = __shfl_sync(full, col, slot * Q + sub_of(xl, yl));
+      if (!has) bits = 0;
       const float2* mrow = s_mean + slot * kNB;
       const float2* orow = s_oc + u * kNB;
       int stop = -1;
-      auto apply = [&](int gi, float v, float c) -> bool {
-        if (!(v >= kAlphaMin)) return false;
-        const float alpha = fminf(kAlphaMax, v);
-        const float Tn = T * (1.f - alpha);
-        if (Tn < kTMin) {
-          stop = gi;
-          return true;
-        }
-        acc += c * alpha * T;
-        T = Tn;
-        return false;
-      };
       while (bits) {
-        const int g0 = __ffs(bits) - 1;
-        bits &= bits - 1u;
-        const bool two = bits != 0u;
-        const int g1 = two ? __ffs(bits) - 1 : g0;
-        bits &= bits - 1u;
+        const int g0 = bits_first(bits);
+        bits &= bits - 1;
+        const bool two = bits != 0;
+        const int g1 = two ? bits_first(bits) : g0;
+        bits &= bits - 1;
         const float4 c0 = s_co[g0];
         const float4 c1 = s_co[g1];
         const float2 u0 = mrow[g0];
@@ -269,8 +267,23 @@ __device__ __forceinline__ void warp_blend_run(const PanelGeom& g, const BlendAr
         const float2 o1 = orow[g1];
         const float v0 = h0 ? o0.x * ex2_approx(p0v) : 0.f;
         const float v1 = h1 ? o1.x * ex2_approx(p1v) : 0.f;
-        if (apply(g0, v0, o0.y)) break;
-        if (apply(g1, v1, o1.y)) break;
+        // both entries in list order without a branch per entry: entry 1
+        // sees the transmittance after entry 0; the stop (rare) branches
+        const bool k0 = v0 >= kAlphaMin, k1 = v1 >= kAlphaMin;
+        const float a0 = fminf(kAlphaMax, v0), a1 = fminf(kAlphaMax, v1);
+        const float T0 = T * (1.f - a0);
+        const float Tb = k0 ? T0 : T;
+        const float T1 = Tb * (1.f - a1);
+        const bool s0 = k0 && T0 < kTMin;
+        const bool s1 = !s0 && k1 && T1 < kTMin;
+        if (k0 && !s0) acc += o0.y * a0 * T;
+        if (s0 || s1) {
+          stop = s0 ? g0 : g1;
+          if (s1) T = Tb;
+          break;
+        }
+        if (k1) acc += o1.y * a1 * Tb;
+        T = k1 ? T1 : Tb;
       }
       const bool alive = has && stop < 0;
       if (has && stop >= 0) {
@@ -315,260 +328,21 @@ __device__ __forceinline__ void warp_blend_run(const PanelGeom& g, const BlendAr
   __syncwarp();  // the warp's shared memory is reused by its next run
 }
 
-// One warp per (cluster, tile) run, wpb warps per block (independent).
+// One warp per (cluster, tile) run, one warp per block: a block's resources
+// are released as soon as its run is done (blocks of several independent
+// warps wait for the slowest one, and hold fewer warps resident).
 template <int Q, bool COUNT>
-__global__ void __launch_bounds__(128) k_blend(PanelGeom g, BlendArgs a, int S, int wpb) {
+__global__ void __launch_bounds__(32) k_blend(PanelGeom g, BlendArgs a, int S) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (a.P_dev && *a.P_dev > a.P_cap) return;  // capacity overflow: leave the image
-  const int warp = threadIdx.x >> 5;
+  // cluster-major: one cluster's attributes stay resident in L2 while its
+  // tiles are blended (tile-major order, a tile's K runs side by side, merges
+  // the runs' partial image sectors in L2 but reads half as much again from
+  // DRAM and was 9 % slower)
   const int nt = a.t_end - a.t_begin;
-  const int64_t run = (int64_t)blockIdx.x * wpb + warp;
-  if (run >= (int64_t)g.K * nt) return;
-  const int k = (int)(run / nt);
-  const int t = a.t_begin + (int)(run - (int64_t)k * nt);
-  unsigned char* ws = smem + (size_t)warp * warp_layout(g.C, S).total;
-  warp_blend_run<Q, COUNT>(g, a, k, t, a.ranges[(size_t)t * g.K + k], ws, S);
-}
-
-// ---- previous blend, kept for side-by-side timing while developing ----
-// Blend of one (tile t, cluster k) run whose list is [rg.x, rg.y). Called by
-// every thread of the block (it synchronises the block); returns uniformly.
-template <int R, bool COUNT>
-__device__ __forceinline__ void blend_run_v1(const PanelGeom& g, const BlendArgs& a, int k, int t,
-                                          uint2 rg, float4* smem) {
-  const int NB = blockDim.x;  // a multiple of 32
-  const int NW = NB >> 5;
-  const int C = g.C;
-  float4* s_co = smem;  // conic * (-log2(e) / 2, -log2(e), -log2(e) / 2), skip threshold
-  float2* s_oc = reinterpret_cast<float2*>(smem + NB);              // [3][NB] (opacity, colour u)
-  float2* s_mean = reinterpret_cast<float2*>(smem + 2 * NB) + NB;   // [C][NB]
-  uint16_t* s_idx = reinterpret_cast<uint16_t*>(s_mean + NB * C);   // [C][NB]
-  int* s_cnt = reinterpret_cast<int*>(s_idx + ((C * NB + 1) & ~1));  // [C][NW + 1]
-
-  const int s0 = a.seg[(size_t)t * (g.K + 1) + k];
-  const int n = a.seg[(size_t)t * (g.K + 1) + k + 1] - s0;
-  if (n <= 0) return;
-  const int tx = t % g.TX, ty = t / g.TX;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
-  // pixel-centre box of the tile, widened by one pixel: a Gaussian whose
-  // region bounding box misses it has alpha < 1/255 on every subpixel here
-  const float bx0 = (float)(tx * g.TW) + 0.5f - 1.f;
-  const float bx1 = (float)min(tx * g.TW + g.TW, g.W) - 0.5f + 1.f;
-  const float by0 = (float)(ty * g.TH) + 0.5f - 1.f;
-  const float by1 = (float)min(ty * g.TH + g.TH, g.H) - 0.5f + 1.f;
-
-  float px[R], py[R], T[R], acc[R];
-  uint32_t stop_at[R];  // list index where the walk stopped
-  int slot[R], ch[R];
-  int64_t oidx[R];
-  bool act[R];
-  unsigned long long n_visit = 0, n_eval = 0;
-#pragma unroll
-  for (int m = 0; m < R; ++m) {
-    const int r = threadIdx.x + m * NB;
-    act[m] = r < n;
-    T[m] = 1.f;
-    acc[m] = 0.f;
-    stop_at[m] = rg.y;
-    px[m] = py[m] = 0.f;
-    slot[m] = 0;
-    ch[m] = 0;
-    oidx[m] = 0;
-    if (act[m]) {
-      const uint32_t e = a.psi[(size_t)t * g.cap + s0 + r];
-      const int view = (int)(e >> 16);
-      const int loc = (int)(e & 0xffffu);
-      const int u = loc % 3;
-      const int xl = (loc / 3) % g.TW;
-      const int yl = (loc / 3) / g.TW;
-      const int x = tx * g.TW + xl, y = ty * g.TH + yl;
-      px[m] = (float)x + 0.5f;
-      py[m] = (float)y + 0.5f;
-      slot[m] = view - k * C;
-      ch[m] = u;
-      oidx[m] = ((int64_t)y * g.W + x) * 3 + u;
-    }
-  }
-  bool live[R];
-#pragma unroll
-  for (int m = 0; m < R; ++m) live[m] = act[m];
-
-  for (uint32_t base = rg.x; base < rg.y; base += (uint32_t)NB) {
-    bool any = false;
-#pragma unroll
-    for (int m = 0; m < R; ++m) any |= act[m];
-    if (!__syncthreads_or(any)) break;
-    // stage one batch: attributes, per-view means and the footprint bits
-    const uint32_t e = base + threadIdx.x;
-    uint32_t mask = 0;
-    if (e < rg.y) {
-      const uint32_t gid = a.list[e];
-      const size_t rec = (size_t)k * a.M + gid;
-      const float4 co = reinterpret_cast<const float4*>(a.conic_opacity)[rec];
-      const float4 ct = reinterpret_cast<const float4*>(a.color_tau)[rec];
-      // w: log2 of the opacity ratio at which alpha reaches 1/255 (skip below)
-      s_co[threadIdx.x] = make_float4(-0.5f * kLog2e * co.x, -kLog2e * co.y, -0.5f * kLog2e * co.z,
-                                      -log2f(255.f * co.w) - 1e-4f);
-      s_oc[threadIdx.x] = make_float2(co.w, ct.x);
-      s_oc[NB + threadIdx.x] = make_float2(co.w, ct.y);
-      s_oc[2 * NB + threadIdx.x] = make_float2(co.w, ct.z);
-      const float det = co.x * co.z - co.y * co.y;
-      const float hx = sqrtf(fmaxf(ct.w * co.z / det, 0.f));
-      const float hy = sqrtf(fmaxf(ct.w * co.x / det, 0.f));
-      const float2* mp = reinterpret_cast<const float2*>(a.means2d) + rec * C;
-      for (int l = 0; l < C; ++l) {
-        const float2 mu = mp[l];
-        s_mean[l * NB + threadIdx.x] = mu;
-        const bool hit = (mu.x + hx >= bx0) && (mu.x - hx <= bx1) && (mu.y + hy >= by0) &&
-                         (mu.y - hy <= by1);
-        mask |= (uint32_t)hit << l;
-      }
-    }
-    // per-view compaction: s_idx[l][..] lists, in list order, the staged
-    // entries whose view-l region meets the tile
-    for (int l = 0; l < C; ++l) {
-      const unsigned b = __ballot_sync(0xffffffffu, (mask >> l) & 1u);
-      if (lane == 0) s_cnt[l * (NW + 1) + warp] = __popc(b);
-    }
-    __syncthreads();
-    if (threadIdx.x < C) {
-      int run = 0;
-      for (int w = 0; w < NW; ++w) {
-        const int c = s_cnt[threadIdx.x * (NW + 1) + w];
-        s_cnt[threadIdx.x * (NW + 1) + w] = run;
-        run += c;
-      }
-      s_cnt[threadIdx.x * (NW + 1) + NW] = run;
-    }
-    __syncthreads();
-    for (int l = 0; l < C; ++l) {
-      const unsigned b = __ballot_sync(0xffffffffu, (mask >> l) & 1u);
-      if ((mask >> l) & 1u) s_idx[l * NB + s_cnt[l * (NW + 1) + warp] + __popc(b & lt)] = (uint16_t)threadIdx.x;
-    }
-    __syncthreads();
-    const int nbatch = (int)min((uint32_t)NB, rg.y - base);
-#pragma unroll
-    for (int m = 0; m < R; ++m) {
-      if (!act[m]) continue;
-      const uint16_t* idx = s_idx + slot[m] * NB;
-      const int cnt = s_cnt[slot[m] * (NW + 1) + NW];
-      int stop = -1, stop_q = -1;
-      const float2* mrow = s_mean + slot[m] * NB;
-      const float2* orow = s_oc + ch[m] * NB;
-      // Entries are taken two at a time: their loads, quadratic forms and
-      // exponentials are independent; the transmittance update stays in
-      // list order, one entry after the other.
-      auto apply = [&](int gi, float v, float c) -> bool {
-        if (!(v >= kAlphaMin)) return false;
-        const float alpha = fminf(kAlphaMax, v);
-        const float Tn = T[m] * (1.f - alpha);
-        if (Tn < kTMin) {
-          act[m] = false;
-          stop = gi;
-          return true;
-        }
-        acc[m] += c * alpha * T[m];
-        T[m] = Tn;
-        return false;
-      };
-      int q = 0;
-      for (; q + 2 <= cnt; q += 2) {
-        const int g0 = idx[q], g1 = idx[q + 1];
-        const float4 c0 = s_co[g0];
-        const float4 c1 = s_co[g1];
-        const float2 u0 = mrow[g0];
-        const float2 u1 = mrow[g1];
-        const float dx0 = px[m] - u0.x, dy0 = py[m] - u0.y;
-        const float dx1 = px[m] - u1.x, dy1 = py[m] - u1.y;
-        const float p0 = quad_power(c0.x, c0.y, c0.z, dx0, dy0);
-        const float p1 = quad_power(c1.x, c1.y, c1.z, dx1, dy1);
-        const bool h0 = p0 <= 0.f && p0 >= c0.w;
-        const bool h1 = p1 <= 0.f && p1 >= c1.w;
-        if (!(h0 || h1)) continue;
-        const float2 o0 = orow[g0];
-        const float2 o1 = orow[g1];
-        const float v0 = h0 ? o0.x * ex2_approx(p0) : 0.f;
-        const float v1 = h1 ? o1.x * ex2_approx(p1) : 0.f;
-        if (apply(g0, v0, o0.y)) {
-          stop_q = q;
-          break;
-        }
-        if (apply(g1, v1, o1.y)) {
-          stop_q = q + 1;
-          break;
-        }
-      }
-      if (stop < 0 && q < cnt) {
-        const int gi = idx[q];
-        const float4 co = s_co[gi];
-        const float2 mu = mrow[gi];
-        const float dx = px[m] - mu.x;
-        const float dy = py[m] - mu.y;
-        const float power = quad_power(co.x, co.y, co.z, dx, dy);
-        if (power <= 0.f && power >= co.w) {
-          const float2 oc = orow[gi];
-          if (apply(gi, oc.x * ex2_approx(power), oc.y)) stop_q = q;
-        }
-      }
-      if (stop >= 0) stop_at[m] = base + (uint32_t)stop;
-      if (COUNT) n_eval += stop_q >= 0 ? (unsigned long long)(stop_q + 1) : (unsigned long long)cnt;
-      // list entries walked in this batch, skipped ones included
-      if (COUNT) n_visit += stop >= 0 ? (unsigned long long)(stop + 1) : (unsigned long long)nbatch;
-    }
-  }
-#pragma unroll
-  for (int m = 0; m < R; ++m) {
-    if (!live[m]) continue;
-    const float bg = ch[m] == 0 ? a.bg[0] : (ch[m] == 1 ? a.bg[1] : a.bg[2]);
-    a.out[oidx[m]] = acc[m] + T[m] * bg;
-    if (a.keep)
-      a.keep[(size_t)t * g.cap + s0 + threadIdx.x + m * NB] = make_uint2(stop_at[m], __float_as_uint(T[m]));
-  }
-  if (COUNT) {
-    unsigned long long cv = n_visit, ce = n_eval;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      cv += __shfl_down_sync(0xffffffffu, cv, o);
-      ce += __shfl_down_sync(0xffffffffu, ce, o);
-    }
-    if (lane == 0) {
-      if (cv) atomicAdd(a.eval_counter, cv);
-      if (ce) atomicAdd(a.eval_counter + 1, ce);
-    }
-  }
-}
-
-
-template <int R, bool COUNT>
-__global__ void __launch_bounds__(256) k_blend_v1(PanelGeom g, BlendArgs a) {
-  extern __shared__ float4 smem4[];
-  if (a.P_dev && *a.P_dev > a.P_cap) return;
-  const int nt = a.t_end - a.t_begin;
-  const int k = blockIdx.x / nt;
-  const int t = a.t_begin + (blockIdx.x - k * nt);
-  blend_run_v1<R, COUNT>(g, a, k, t, a.ranges[(size_t)t * g.K + k], smem4);
-}
-size_t blend_smem_bytes_v1(int C, int block) {
-  const int nw = block / 32;
-  return (size_t)block * (sizeof(float4) + 3 * sizeof(float2) + C * sizeof(float2)) +
-         (((size_t)C * block + 1) & ~(size_t)1) * sizeof(uint16_t) + (size_t)C * (nw + 1) * sizeof(int);
-}
-template <int R>
-cudaError_t launch_r_v1(const PanelGeom& g, const BlendArgs& a, int block, cudaStream_t s) {
-  const size_t smem = blend_smem_bytes_v1(g.C, block);
-  const unsigned grid = (unsigned)((int64_t)g.K * (a.t_end - a.t_begin));
-  if (a.eval_counter) {
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(k_blend_v1<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_blend_v1<R, true><<<grid, block, smem, s>>>(g, a);
-  } else {
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(k_blend_v1<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_blend_v1<R, false><<<grid, block, smem, s>>>(g, a);
-  }
-  note_launches(1);
-  return cudaGetLastError();
+  const int k = (int)(blockIdx.x / (unsigned)nt);
+  const int t = a.t_begin + (int)(blockIdx.x - (unsigned)k * (unsigned)nt);
+  warp_blend_run<Q, COUNT>(g, a, k, t, a.ranges[(size_t)t * g.K + k], smem, S);
 }
 
 // Batched form: every warp of a grid sized to the GPU pulls (scene, cluster,
@@ -598,31 +372,23 @@ __global__ void __launch_bounds__(256) k_blend_batch(BatchBlendArgs b, int S, in
 
 // subpixel capacity of a warp for runs of up to max_segment subpixels
 inline int warp_capacity(int max_segment) { return ((max(max_segment, 1) + 7) / 8) * 8; }
-// warps per block: one (a block's resources are released as soon as its run
-// is done, instead of waiting for sibling warps with longer runs)
+// warps per block of the persistent batched blend (its warps pull runs until
+// none are left, so they finish together)
 inline int warps_per_block(size_t per_warp) {
-  (void)per_warp;
-  return 1;
+  return per_warp <= 12 * 1024 ? 4 : (per_warp <= 24 * 1024 ? 2 : 1);
 }
 
 template <int Q, bool COUNT>
 cudaError_t launch_q(const PanelGeom& g, const BlendArgs& a, cudaStream_t s) {
   const int S = warp_capacity(a.max_segment);
-  const size_t per = warp_layout(g.C, S).total;
-  int wpb = warps_per_block(per);
-  {
-    const char* e = getenv("LFD_BLEND_WPB");
-    if (e && (e[0] == '1' || e[0] == '2' || e[0] == '4')) wpb = e[0] - '0';
-  }
-  const size_t smem = per * (size_t)wpb;
+  const size_t smem = warp_layout(g.C, S).total;  // one warp per block
   if (smem > 48 * 1024) {
     const cudaError_t e =
         cudaFuncSetAttribute(k_blend<Q, COUNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   const int64_t runs = (int64_t)g.K * (a.t_end - a.t_begin);
-  const unsigned grid = (unsigned)((runs + wpb - 1) / wpb);
-  k_blend<Q, COUNT><<<grid, 32 * wpb, smem, s>>>(g, a, S, wpb);
+  k_blend<Q, COUNT><<<(unsigned)runs, 32, smem, s>>>(g, a, S);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -659,15 +425,8 @@ cudaError_t launch_blend_batch(const BatchBlendArgs& b, int max_segment, int C_m
   if (b.total_runs == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(b.work, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
-  const int Q = blend_subtiles(C_max);
-  if (Q == 4) return launch_batch_q<4>(b, max_segment, C_max, s);
-  if (Q == 2) return launch_batch_q<2>(b, max_segment, C_max, s);
-  return launch_batch_q<1>(b, max_segment, C_max, s);
-}
-
-static int blend_v1_selected() {
-  const char* s = getenv("LFD_BLEND_V1");
-  return (s && s[0] == '1') ? 1 : 0;
+  return blend_subtiles(C_max) == 2 ? launch_batch_q<2>(b, max_segment, C_max, s)
+                                    : launch_batch_q<1>(b, max_segment, C_max, s);
 }
 
 cudaError_t launch_blend(const PanelGeom& g, const BlendArgs& args, cudaStream_t s) {
@@ -677,32 +436,9 @@ cudaError_t launch_blend(const PanelGeom& g, const BlendArgs& args, cudaStream_t
   if (g.K == 0 || a.t_end <= a.t_begin) return cudaSuccess;
   const int need = a.max_segment > 0 ? a.max_segment : 1;
   if (need > kMaxTileSubpixels) return cudaErrorInvalidValue;
-  if (blend_v1_selected()) {
-    int R = 2;
-    if (a.subpixels_per_thread > 0 && (need + a.subpixels_per_thread - 1) / a.subpixels_per_thread <= 256)
-      R = a.subpixels_per_thread;
-    while (R < 8 && (need + R - 1) / R > 256) R *= 2;
-    int block = ((need + R - 1) / R + 31) / 32 * 32;
-    switch (R) {
-      case 1: return launch_r_v1<1>(g, a, block, s);
-      case 2: return launch_r_v1<2>(g, a, block, s);
-      case 4: return launch_r_v1<4>(g, a, block, s);
-      default: return launch_r_v1<8>(g, a, block, s);
-    }
-  }
-  int Q = blend_subtiles(g.C);
-  {
-    const char* e = getenv("LFD_BLEND_Q");
-    if (e && (e[0] == '1' || e[0] == '2' || e[0] == '4') && g.C * (e[0] - '0') <= 32) Q = e[0] - '0';
-  }
-  if (a.eval_counter) {
-    if (Q == 4) return launch_q<4, true>(g, a, s);
-    if (Q == 2) return launch_q<2, true>(g, a, s);
-    return launch_q<1, true>(g, a, s);
-  }
-  if (Q == 4) return launch_q<4, false>(g, a, s);
-  if (Q == 2) return launch_q<2, false>(g, a, s);
-  return launch_q<1, false>(g, a, s);
+  const int Q = blend_subtiles(g.C);
+  if (a.eval_counter) return Q == 2 ? launch_q<2, true>(g, a, s) : launch_q<1, true>(g, a, s);
+  return Q == 2 ? launch_q<2, false>(g, a, s) : launch_q<1, false>(g, a, s);
 }
 
 }  // namespace lfd
