@@ -2,7 +2,7 @@
 // the Gaussian-tile pairs are sorted so that every (tile, cluster) list is
 // contiguous and depth-ordered; Alg. 1 stage 3).
 //
-// Radix sort: reduce-then-scan per 8-bit digit. Pass = (1) per-tile digit
+// Radix sort: reduce-then-scan per digit (8 or 9 bits). Pass = (1) per-tile digit
 // histogram into a digit-major table, (2) exclusive scan of that table, which
 // yields every tile's global output base per digit, (3) stable scatter. The
 // scatter kernel is persistent: each block walks its share of the tiles and,
@@ -119,13 +119,20 @@ __global__ void __launch_bounds__(kScanThreads)
   }
 }
 
-constexpr int kRadixBits = 8;
-constexpr int kRadix = 1 << kRadixBits;
+// Digit width per key type: 8 bits for the 32-bit pair keys (the 14 tile
+// bits of a 4K panel take two passes either way), 9 bits for the 64-bit keys
+// (the 35-bit (cluster, depth) item keys take four passes instead of five).
+template <typename K>
+struct RadixOf {
+  static constexpr int bits = sizeof(K) == 8 ? 9 : 8;
+  static constexpr int radix = 1 << bits;
+};
+constexpr int kMaxRadix = 512;
 constexpr int kSortThreads = 512;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortRounds = 8;
 constexpr int kSortTile = kSortThreads * kSortRounds;  // 4096 items
-static_assert(kSortThreads >= kRadix, "one thread per digit in the digit phases");
+static_assert(kSortThreads >= kMaxRadix, "one thread per digit in the digit phases");
 
 template <typename K>
 __device__ __forceinline__ int digit_of(K key, int shift, int mask) {
@@ -146,6 +153,7 @@ template <typename K>
 __global__ void __launch_bounds__(kSortThreads)
     k_rts_hist(const K* __restrict__ keys, int64_t n_cap, const unsigned long long* __restrict__ n_dev,
                int shift, int mask, uint32_t* __restrict__ hist, int64_t nb) {
+  constexpr int kRadix = RadixOf<K>::radix;
   __shared__ uint32_t s_h[kSortWarps][kRadix];
   const int warp = threadIdx.x >> 5;
   for (int a = threadIdx.x; a < kSortWarps * kRadix; a += kSortThreads) (&s_h[0][0])[a] = 0;
@@ -202,6 +210,7 @@ __global__ void __launch_bounds__(kSortThreads)
                   uint32_t* __restrict__ vout, int64_t n_cap, const unsigned long long* __restrict__ n_dev,
                   int shift, int mask, const uint32_t* __restrict__ hscan, int64_t nb,
                   uint32_t* __restrict__ err) {
+  constexpr int kRadix = RadixOf<K>::radix;
   extern __shared__ __align__(128) unsigned char s_raw[];
   // [in0 keys][in0 vals][in1 keys][in1 vals][out keys][out vals]
   constexpr size_t kBuf = (size_t)kSortTile * (sizeof(K) + sizeof(uint32_t));
@@ -363,6 +372,7 @@ cudaError_t radix_sort_impl(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals
   *result_in_alt = false;
   if (n_cap <= 1 || end_bit <= begin_bit) return cudaSuccess;
   const int64_t nb = (n_cap + kSortTile - 1) / kSortTile;
+  constexpr int kRadix = RadixOf<K>::radix;
   uint32_t* hist = reinterpret_cast<uint32_t*>(temp);
   uint32_t* hscan = hist + nb * kRadix;
   void* stemp = hscan + nb * kRadix;
@@ -378,6 +388,7 @@ cudaError_t radix_sort_impl(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals
   uint32_t* src_v = vals;
   uint32_t* dst_v = vals_alt;
   bool alt = false;
+  constexpr int kRadixBits = RadixOf<K>::bits;
   for (int shift = begin_bit; shift < end_bit; shift += kRadixBits) {
     const int nbits = end_bit - shift < kRadixBits ? end_bit - shift : kRadixBits;
     const int mask = (1 << nbits) - 1;
@@ -434,7 +445,7 @@ cudaError_t scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, void* t
 
 size_t radix_temp_bytes(int64_t n) {
   const int64_t nb = (n + kSortTile - 1) / kSortTile;
-  return (size_t)nb * kRadix * 2 * sizeof(uint32_t) + scan_temp_bytes(nb * kRadix) +
+  return (size_t)nb * kMaxRadix * 2 * sizeof(uint32_t) + scan_temp_bytes(nb * kMaxRadix) +
          sizeof(unsigned long long) + 256;
 }
 
