@@ -119,9 +119,13 @@ __global__ void __launch_bounds__(kScanThreads)
   }
 }
 
-// Digit width per key type: 8 bits for the 32-bit pair keys (the 14 tile
-// bits of a 4K panel take two passes either way), 9 bits for the 64-bit keys
-// (the 35-bit (cluster, depth) item keys take four passes instead of five).
+// Widest digit per key type: 8 bits for the 32-bit pair keys, 9 bits for the
+// 64-bit keys (the 35-bit (cluster, depth) item keys take four passes instead
+// of five). A sort takes the fewest passes these widths allow and spreads the
+// key bits evenly over them: the 14 tile bits of a 4K panel go in two 7-bit
+// passes, whose 128 output runs per 4096-item tile are twice as long as 256
+// runs would be (the scatter's stores coalesce better; the digit tables are
+// half as large).
 template <typename K>
 struct RadixOf {
   static constexpr int bits = sizeof(K) == 8 ? 9 : 8;
@@ -188,7 +192,7 @@ __global__ void __launch_bounds__(kSortThreads)
   }
   __syncthreads();
   const int d = threadIdx.x;
-  if (d < kRadix) {
+  if (d <= mask) {
     uint32_t sum = 0;
 #pragma unroll
     for (int w = 0; w < kSortWarps; ++w) sum += s_h[w][d];
@@ -259,7 +263,7 @@ __global__ void __launch_bounds__(kSortThreads)
     const int64_t tile0 = tile * kSortTile;
     const int cnt = (int)min((int64_t)kSortTile, n - tile0);
     for (int a = threadIdx.x; a < kSortWarps * kRadix; a += kSortThreads) (&s_wcnt[0][0])[a] = 0;
-    if (d < kRadix) s_base[d] = hscan[(int64_t)d * nb + tile];
+    if (d <= mask) s_base[d] = hscan[(int64_t)d * nb + tile];
     if (threadIdx.x == 0) fetch(b ^ 1, tile + gridDim.x);
     if (is_full(tile)) {
       const uint32_t ph = (parity >> b) & 1u;
@@ -389,13 +393,15 @@ cudaError_t radix_sort_impl(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals
   uint32_t* dst_v = vals_alt;
   bool alt = false;
   constexpr int kRadixBits = RadixOf<K>::bits;
-  for (int shift = begin_bit; shift < end_bit; shift += kRadixBits) {
-    const int nbits = end_bit - shift < kRadixBits ? end_bit - shift : kRadixBits;
+  const int passes = (end_bit - begin_bit + kRadixBits - 1) / kRadixBits;
+  const int width = (end_bit - begin_bit + passes - 1) / passes;
+  for (int shift = begin_bit; shift < end_bit; shift += width) {
+    const int nbits = end_bit - shift < width ? end_bit - shift : width;
     const int mask = (1 << nbits) - 1;
     k_rts_hist<K><<<(unsigned)nb, kSortThreads, 0, s>>>(src_k, n_cap, n_dev, shift, mask, hist, nb);
     note_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = scan_exclusive(hist, hscan, nb * kRadix, stemp, total, s)) != cudaSuccess) return e;
+    if ((e = scan_exclusive(hist, hscan, nb * (mask + 1), stemp, total, s)) != cudaSuccess) return e;
     k_rts_scatter<K><<<(unsigned)grid, kSortThreads, smem, s>>>(src_k, dst_k, src_v, dst_v, n_cap,
                                                                 n_dev, shift, mask, hscan, nb, err);
     note_launches(1);

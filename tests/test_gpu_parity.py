@@ -129,7 +129,10 @@ def _stage_inputs(w, scene, cams, c):
     return f32_attrs(proj, c)
 
 
-@pytest.mark.parametrize("sort_mode", [lfd.SORT_DEPTH_FIRST, lfd.SORT_KEY64])
+ALL_SORT_MODES = [lfd.SORT_DEPTH_FIRST, lfd.SORT_KEY64]
+
+
+@pytest.mark.parametrize("sort_mode", ALL_SORT_MODES)
 @pytest.mark.parametrize("tile,c", [((16, 16), 8), ((8, 8), 1), ((32, 16), 3), ((16, 8), 5)])
 def test_bins_sort_ranges_bit_exact(tiny, sort_mode, tile, c):
     w, scene, cams = tiny
@@ -148,25 +151,35 @@ def test_bins_sort_ranges_bit_exact(tiny, sort_mode, tile, c):
     plan.close()
 
 
-def test_bins_random_conics_bit_exact():
+# (width, height, tile, largest sigma, Gaussians per cluster): the second panel
+# has more than 64 tile columns and 15 tile rows, so the largest ellipses
+# overflow the count pass's union descriptor (their units come from the
+# geometry) and span several 64-column windows
+@pytest.mark.parametrize("width,height,tile,smax,m", [(200, 120, (16, 16), 30.0, 3000),
+                                                      (1100, 330, (8, 8), 160.0, 1500)])
+def test_bins_random_conics_bit_exact(width, height, tile, smax, m):
     # synthetic ellipses of every orientation and size, many off-panel
-    panel = synth.Panel(200, 120, 12, 0.15, 5.0, 0.0)
-    K, M, C = 3, 3000, 4
+    panel = synth.Panel(width, height, 12, 0.15, 5.0, 0.0)
+    K, M, C = 3, m, 4
     rng = np.random.default_rng(31)
-    conic = synth.random_conics(K * M, 32, 0.6, 30.0).reshape(K, M, 3)
+    conic = synth.random_conics(K * M, 32, 0.6, smax).reshape(K, M, 3)
     tau = rng.uniform(0, 11.0, (K, M)).astype(np.float32)
     tau[rng.uniform(size=(K, M)) < 0.1] = -1.0
     depth = rng.uniform(0.3, 40.0, (K, M)).astype(np.float32)
-    base = np.stack([rng.uniform(-40, 240, (K, M)), rng.uniform(-40, 160, (K, M))], -1)
+    base = np.stack([rng.uniform(-40, width + 40, (K, M)), rng.uniform(-40, height + 40, (K, M))], -1)
     means = (base[:, :, None, :] + rng.normal(0, 10.0, (K, M, C, 2))).astype(np.float32)
     means[rng.uniform(size=(K, M, C)) < 0.05] = np.nan
     co = np.concatenate([conic, np.full((K, M, 1), 0.5, np.float32)], -1)
     ct_ = np.concatenate([np.full((K, M, 3), 0.5, np.float32), tau[..., None]], -1)
     attrs = {"means2d": means, "conic_opacity": co, "color_tau": ct_, "depth": depth}
-    for sort_mode in (lfd.SORT_DEPTH_FIRST, lfd.SORT_KEY64):
-        plan = lfd.Plan(panel, tile=(16, 16), views_per_cluster=C, sort_mode=sort_mode)
+    ref = oracle.mirror_lists(panel.width, panel.height, tile, conic, tau, depth, means)
+    if width > 1000:
+        # the case reaches the overflow path: unions wider than 64 tile columns
+        counts = np.asarray(ref["counts"]).reshape(K, M)
+        assert (counts > 15 * 64).sum() > 10
+    for sort_mode in ALL_SORT_MODES:
+        plan = lfd.Plan(panel, tile=tile, views_per_cluster=C, sort_mode=sort_mode)
         _img, st = plan.render_projected(to_dev(attrs))
-        ref = oracle.mirror_lists(panel.width, panel.height, (16, 16), conic, tau, depth, means)
         lst, ranges, keys = plan.lists(st["num_pairs"], with_keys=sort_mode == lfd.SORT_KEY64)
         assert st["num_pairs"] == len(ref["list"])
         np.testing.assert_array_equal(lst, ref["list"])
@@ -203,7 +216,7 @@ def test_blend_matches_oracle_on_same_lists(tiny, c):
 
 
 @pytest.mark.parametrize("c", [1, 3, 8])
-@pytest.mark.parametrize("sort_mode", [lfd.SORT_DEPTH_FIRST, lfd.SORT_KEY64])
+@pytest.mark.parametrize("sort_mode", ALL_SORT_MODES)
 def test_render_matches_fp64_oracle(tiny, c, sort_mode):
     w, scene, cams = tiny
     plan = lfd.Plan(w.panel, views_per_cluster=c, sort_mode=sort_mode)
@@ -432,3 +445,24 @@ def test_paper4k_sampled_crops(paper4k_oracle, tile):
         ref, lo, hi = oracle.render_bracket(proj, V, c, crop=crop, mode=1)
         assert_render_matches(got[y0:y0 + ch, x0:x0 + cw], ref, lo, hi, f"crop {crop}")
     plan.close()
+
+
+def test_depth_first_lists_equal_eq11_key_sort_on_4k():
+    # the paper4k panel at full size (300k Gaussians, 32x16 tiles): sorting the
+    # depths once and the emitted pairs by their tile bits gives the same list,
+    # ranges and image as sorting the 64-bit keys of Eq. 11
+    w = synth.WORKLOADS["paper4k"]
+    scene = lfd.scene_to_device(synth.scene_for(w, 300_000))
+    cams = synth.arc_cameras(w.rig, w.panel.width, w.panel.height)
+    got = {}
+    for mode in (lfd.SORT_DEPTH_FIRST, lfd.SORT_KEY64):
+        plan = lfd.Plan(w.panel, tile=(32, 16), views_per_cluster=8, sort_mode=mode)
+        img, st = plan.render(scene, cams)
+        lst, ranges, _ = plan.lists(st["num_pairs"])
+        got[mode] = (img.cpu(), lst, ranges, st["num_pairs"])
+        plan.close()
+    a, b = got[lfd.SORT_DEPTH_FIRST], got[lfd.SORT_KEY64]
+    assert a[3] == b[3] > 10_000_000
+    np.testing.assert_array_equal(a[2], b[2])
+    np.testing.assert_array_equal(a[1], b[1])
+    assert torch.equal(a[0], b[0])
