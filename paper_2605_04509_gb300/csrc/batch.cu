@@ -235,48 +235,41 @@ int lfd_batch_render(lfd_batch* b, const lfd_gaussians* scenes, const lfd_camera
   uint64_t* ik = b->item_key[0].as<uint64_t>();
   uint32_t* iv = b->item_val[0].as<uint32_t>();
   unsigned char* desc = b->bin_desc.as<unsigned char>();
-  // projection (Eq. 5-6) and item keys, per scene
+  // projection (Eq. 5-6), per scene (each with its own camera table)
+  BatchBins bb{};
+  bb.n_scenes = b->n;
   for (int s = 0; s < b->n; ++s) {
-    const int64_t M = scenes[s].count;
     int rc = lfd_project(b->plans[s], &scenes[s], cams[s], b->g[s].N, b->proj_means[s].as<float>(),
                          b->proj_co[s].as<float>(), b->proj_ct[s].as<float>(),
                          b->proj_depth[s].as<float>(), stream);
     if (rc != LFD_OK) return rc;
-    if (M == 0) continue;
-    B_CUDA(launch_item_keys(b->g[s], M, b->proj_depth[s].as<float>(), b->proj_ct[s].as<float>(),
-                            ik + item_off[s], iv + item_off[s], st));
+    SceneBins& sb = bb.sc[s];
+    sb.g = b->g[s];
+    sb.M = scenes[s].count;
+    sb.n = item_off[s + 1] - item_off[s];
+    sb.off = item_off[s];
+    sb.means2d = b->proj_means[s].as<float>();
+    sb.conic_opacity = b->proj_co[s].as<float>();
+    sb.color_tau = b->proj_ct[s].as<float>();
+    sb.depth = b->proj_depth[s].as<float>();
   }
-  // one (global cluster, depth) sort of all items; scene s's items then hold
-  // positions [item_off[s], item_off[s + 1]) with scene-local indices
+  // key generation of all scenes, one launch per pass: item keys, one
+  // (global cluster, depth) sort of all items (scene s's items then hold
+  // positions [item_off[s], item_off[s + 1]) with scene-local indices), the
+  // emission positions, counts and descriptors there, their scan, emission
+  B_CUDA(launch_item_keys_batch(bb, ik, iv, st));
   bool alt = false;
   B_CUDA(radix_sort_u64(ik, b->item_key[1].as<uint64_t>(), iv, b->item_val[1].as<uint32_t>(), n_items,
                         nullptr, 0, 32 + b->bit_cluster, b->radix_tmp.p, &alt, d_err, st));
   const uint32_t* order = b->item_val[alt ? 1 : 0].as<uint32_t>();
-  for (int s = 0; s < b->n; ++s) {
-    const int64_t M = scenes[s].count;
-    const int64_t n = (int64_t)b->g[s].K * M;
-    if (n == 0) continue;
-    // counts and descriptors written at each item's emission position
-    B_CUDA(launch_invert_u32(order + item_off[s], n, b->emit_pos.as<uint32_t>() + item_off[s], st));
-    B_CUDA(launch_bin_count(b->g[s], M, b->proj_means[s].as<float>(), b->proj_co[s].as<float>(),
-                            b->proj_ct[s].as<float>(), nullptr, b->emit_pos.as<uint32_t>() + item_off[s],
-                            n, b->counts.as<uint32_t>() + item_off[s],
-                            desc + (size_t)item_off[s] * kBinDescBytes, st));
-  }
+  B_CUDA(launch_invert_batch(bb, order, b->emit_pos.as<uint32_t>(), st));
+  B_CUDA(launch_bin_count_batch(bb, b->emit_pos.as<uint32_t>(), b->counts.as<uint32_t>(), desc, st));
   B_CUDA(scan_exclusive(b->counts.as<uint32_t>(), b->offsets.as<uint32_t>(), n_items, b->scan_tmp.p,
                         d_small, st));
   const unsigned long long P = (unsigned long long)b->cap_P;
-  for (int s = 0; s < b->n; ++s) {
-    const int64_t M = scenes[s].count;
-    const int64_t n = (int64_t)b->g[s].K * M;
-    if (n == 0) continue;
-    B_CUDA(launch_bin_emit_coop(b->g[s], M, b->proj_means[s].as<float>(), b->proj_co[s].as<float>(),
-                                b->proj_ct[s].as<float>(), b->proj_depth[s].as<float>(),
-                                order + item_off[s], n, b->counts.as<uint32_t>() + item_off[s],
-                                b->offsets.as<uint32_t>() + item_off[s],
-                                b->pair_key[0].as<uint32_t>(), nullptr, b->pair_val[0].as<uint32_t>(),
-                                desc + (size_t)item_off[s] * kBinDescBytes, d_small, P, d_err, st));
-  }
+  B_CUDA(launch_bin_emit_batch(bb, order, b->counts.as<uint32_t>(), b->offsets.as<uint32_t>(),
+                               b->pair_key[0].as<uint32_t>(), b->pair_val[0].as<uint32_t>(), desc,
+                               d_small, P, d_err, st));
   // one stable sort on the tile bits: (tile, scene, cluster, depth)
   alt = false;
   const int low = b->bit_s + b->bit_kc;

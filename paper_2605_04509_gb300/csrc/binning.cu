@@ -245,14 +245,18 @@ constexpr int kBinWarps = 4;
 // boxes of one view hit consecutive words (no bank conflicts).
 constexpr int kBoxFields = 6;  // mx, my, bx0, bx1, y0, y1 (y0 > y1: not seen)
 
-__global__ void __launch_bounds__(32 * kBinWarps)
-    k_bin_count(PanelGeom g, int64_t M, const float2* __restrict__ means2d,
-                const float4* __restrict__ conic_opacity, const float4* __restrict__ color_tau,
-                const uint32_t* __restrict__ order, const uint32_t* __restrict__ dest,
-                int64_t n_items, uint32_t* __restrict__ counts, BinDesc* __restrict__ desc) {
+// One block of the count pass: items [blk * 32 kBinWarps, ...) of one scene.
+__device__ __forceinline__ void bin_count_block(const PanelGeom& g, int64_t M,
+                                                const float2* __restrict__ means2d,
+                                                const float4* __restrict__ conic_opacity,
+                                                const float4* __restrict__ color_tau,
+                                                const uint32_t* __restrict__ order,
+                                                const uint32_t* __restrict__ dest, int64_t n_items,
+                                                uint32_t* __restrict__ counts,
+                                                BinDesc* __restrict__ desc, int64_t blk) {
   __shared__ uint32_t s_n[kBinWarps][32];
   extern __shared__ float s_box[];  // [kBoxFields][C][32 * kBinWarps]
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t s = blk * (32 * kBinWarps) + threadIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool in = s < n_items;
   uint32_t r = 0;
@@ -344,6 +348,33 @@ __global__ void __launch_bounds__(32 * kBinWarps)
   }
 }
 
+__global__ void __launch_bounds__(32 * kBinWarps)
+    k_bin_count(PanelGeom g, int64_t M, const float2* __restrict__ means2d,
+                const float4* __restrict__ conic_opacity, const float4* __restrict__ color_tau,
+                const uint32_t* __restrict__ order, const uint32_t* __restrict__ dest,
+                int64_t n_items, uint32_t* __restrict__ counts, BinDesc* __restrict__ desc) {
+  bin_count_block(g, M, means2d, conic_opacity, color_tau, order, dest, n_items, counts, desc,
+                  blockIdx.x);
+}
+
+// Scene of block blk of a folded batch launch (scenes own consecutive blocks).
+__device__ __forceinline__ int scene_of_block(const BatchBins& bb, uint32_t blk) {
+  int s = 0;
+  while (s + 1 < bb.n_scenes && blk >= bb.sc[s + 1].blk_off) ++s;
+  return s;
+}
+
+// The count pass of every scene of a batch in one launch.
+__global__ void __launch_bounds__(32 * kBinWarps)
+    k_bin_count_batch(BatchBins bb, const uint32_t* __restrict__ dest, uint32_t* __restrict__ counts,
+                      BinDesc* __restrict__ desc) {
+  const SceneBins& sc = bb.sc[scene_of_block(bb, blockIdx.x)];
+  bin_count_block(sc.g, sc.M, reinterpret_cast<const float2*>(sc.means2d),
+                  reinterpret_cast<const float4*>(sc.conic_opacity),
+                  reinterpret_cast<const float4*>(sc.color_tau), nullptr, dest + sc.off, sc.n,
+                  counts + sc.off, desc + sc.off, blockIdx.x - sc.blk_off);
+}
+
 __global__ void k_bin_emit(PanelGeom g, int64_t M, const float2* __restrict__ means2d,
                            const float4* __restrict__ conic_opacity,
                            const float4* __restrict__ color_tau, const float* __restrict__ depth,
@@ -415,22 +446,22 @@ struct EmitCap {
   static constexpr int value = (6144 / (int)(sizeof(KeyT) + 4)) & ~31;  // ~24 KB per block
 };
 
+// One block of the emit pass: items [blk * 32 kEmitWarps, ...) of one scene.
 template <typename KeyT>
-__global__ void __launch_bounds__(32 * kEmitWarps)
-    k_bin_emit_staged(PanelGeom g, int64_t M, const float2* __restrict__ means2d,
-                      const float4* __restrict__ conic_opacity, const float4* __restrict__ color_tau,
-                      const float* __restrict__ depth, const uint32_t* __restrict__ order,
-                      int64_t n_items, const uint32_t* __restrict__ counts,
-                      const uint32_t* __restrict__ offsets, KeyT* __restrict__ keys,
-                      uint32_t* __restrict__ vals, const BinDesc* __restrict__ desc,
-                      const unsigned long long* __restrict__ P_dev, unsigned long long P_cap,
-                      uint32_t* __restrict__ err) {
+__device__ __forceinline__ void bin_emit_block(
+    const PanelGeom& g, int64_t M, const float2* __restrict__ means2d,
+    const float4* __restrict__ conic_opacity, const float4* __restrict__ color_tau,
+    const float* __restrict__ depth, const uint32_t* __restrict__ order, int64_t n_items,
+    const uint32_t* __restrict__ counts, const uint32_t* __restrict__ offsets, KeyT* __restrict__ keys,
+    uint32_t* __restrict__ vals, const BinDesc* __restrict__ desc,
+    const unsigned long long* __restrict__ P_dev, unsigned long long P_cap, uint32_t* __restrict__ err,
+    int64_t blk) {
   constexpr int CAP = EmitCap<KeyT>::value;
   constexpr bool kWide = sizeof(KeyT) == 8;
   __shared__ KeyT s_key[kEmitWarps][CAP];
   __shared__ uint32_t s_val[kEmitWarps][CAP];
   __shared__ __align__(16) unsigned long long s_desc[kEmitWarps][32][kDescRows + 1];
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t s = blk * (32 * kEmitWarps) + threadIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (P_dev && *P_dev > P_cap) {  // more pairs than the buffers hold: write nothing
     if (s == 0) atomicOr(err, 2u);
@@ -524,6 +555,65 @@ __global__ void __launch_bounds__(32 * kEmitWarps)
       vals[wbase + q] = s_val[warp][q];
     }
   }
+}
+
+template <typename KeyT>
+__global__ void __launch_bounds__(32 * kEmitWarps)
+    k_bin_emit_staged(PanelGeom g, int64_t M, const float2* __restrict__ means2d,
+                      const float4* __restrict__ conic_opacity, const float4* __restrict__ color_tau,
+                      const float* __restrict__ depth, const uint32_t* __restrict__ order,
+                      int64_t n_items, const uint32_t* __restrict__ counts,
+                      const uint32_t* __restrict__ offsets, KeyT* __restrict__ keys,
+                      uint32_t* __restrict__ vals, const BinDesc* __restrict__ desc,
+                      const unsigned long long* __restrict__ P_dev, unsigned long long P_cap,
+                      uint32_t* __restrict__ err) {
+  bin_emit_block<KeyT>(g, M, means2d, conic_opacity, color_tau, depth, order, n_items, counts,
+                       offsets, keys, vals, desc, P_dev, P_cap, err, blockIdx.x);
+}
+
+// The emit pass of every scene of a batch in one launch (32-bit pair keys);
+// counts, offsets and descriptors indexed by batch position, order by scene
+// position (scene-local item indices).
+__global__ void __launch_bounds__(32 * kEmitWarps)
+    k_bin_emit_batch(BatchBins bb, const uint32_t* __restrict__ order,
+                     const uint32_t* __restrict__ counts, const uint32_t* __restrict__ offsets,
+                     uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                     const BinDesc* __restrict__ desc, const unsigned long long* __restrict__ P_dev,
+                     unsigned long long P_cap, uint32_t* __restrict__ err) {
+  const SceneBins& sc = bb.sc[scene_of_block(bb, blockIdx.x)];
+  bin_emit_block<uint32_t>(sc.g, sc.M, reinterpret_cast<const float2*>(sc.means2d),
+                           reinterpret_cast<const float4*>(sc.conic_opacity),
+                           reinterpret_cast<const float4*>(sc.color_tau), sc.depth, order + sc.off,
+                           sc.n, counts + sc.off, offsets + sc.off, keys, vals, desc + sc.off, P_dev,
+                           P_cap, err, blockIdx.x - sc.blk_off);
+}
+
+// Item keys of every scene of a batch: item p of the batch arrays is item
+// p - off of its scene (keys with the scene's global clusters, values local).
+__global__ void k_item_keys_batch(BatchBins bb, int64_t n_total, uint64_t* __restrict__ keys,
+                                  uint32_t* __restrict__ vals) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_total) return;
+  int s = 0;
+  while (s + 1 < bb.n_scenes && p >= bb.sc[s + 1].off) ++s;
+  const SceneBins& sc = bb.sc[s];
+  const int64_t r = p - sc.off;
+  const uint64_t k = (uint64_t)((uint32_t)r / (uint32_t)sc.M);
+  const float tau = reinterpret_cast<const float4*>(sc.color_tau)[r].w;
+  const uint32_t d = tau >= 0.f ? __float_as_uint(sc.depth[r]) : 0xffffffffu;
+  keys[p] = ((k + (uint64_t)sc.g.cluster_base) << 32) | d;
+  vals[p] = (uint32_t)r;
+}
+
+// Per scene, inv[off + perm[p]] = p - off for the scene's batch positions p.
+__global__ void k_invert_batch(BatchBins bb, int64_t n_total, const uint32_t* __restrict__ perm,
+                               uint32_t* __restrict__ inv) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_total) return;
+  int s = 0;
+  while (s + 1 < bb.n_scenes && p >= bb.sc[s + 1].off) ++s;
+  const int64_t off = bb.sc[s].off;
+  inv[off + perm[p]] = (uint32_t)(p - off);
 }
 
 __global__ void k_gather_u32(const uint32_t* __restrict__ src, const uint32_t* __restrict__ idx,
@@ -671,6 +761,70 @@ cudaError_t launch_bin_emit_coop(const PanelGeom& g, int64_t M, const float* mea
         reinterpret_cast<const float4*>(conic_opacity), reinterpret_cast<const float4*>(color_tau),
         depth, order, n_items, counts, offsets, keys32, vals,
         reinterpret_cast<const BinDesc*>(desc), P_dev, P_cap, err);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+// Block offsets of the scenes for a launch of `threads` items per block;
+// returns the total block count.
+inline uint32_t place_blocks(BatchBins& bb, int threads) {
+  uint32_t b = 0;
+  for (int i = 0; i < bb.n_scenes; ++i) {
+    bb.sc[i].blk_off = b;
+    b += (uint32_t)((bb.sc[i].n + threads - 1) / threads);
+  }
+  return b;
+}
+
+inline int64_t batch_items(const BatchBins& bb) {
+  return bb.n_scenes ? bb.sc[bb.n_scenes - 1].off + bb.sc[bb.n_scenes - 1].n : 0;
+}
+
+cudaError_t launch_item_keys_batch(const BatchBins& bb, uint64_t* keys, uint32_t* vals, cudaStream_t s) {
+  const int64_t n = batch_items(bb);
+  if (n == 0) return cudaSuccess;
+  k_item_keys_batch<<<blocks_for(n, 256), 256, 0, s>>>(bb, n, keys, vals);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_invert_batch(const BatchBins& bb, const uint32_t* perm, uint32_t* inv, cudaStream_t s) {
+  const int64_t n = batch_items(bb);
+  if (n == 0) return cudaSuccess;
+  k_invert_batch<<<blocks_for(n, 256), 256, 0, s>>>(bb, n, perm, inv);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bin_count_batch(const BatchBins& bb_in, const uint32_t* dest, uint32_t* counts, void* desc,
+                                   cudaStream_t s) {
+  BatchBins bb = bb_in;
+  const uint32_t blocks = place_blocks(bb, 32 * kBinWarps);
+  if (blocks == 0) return cudaSuccess;
+  int C_max = 1;
+  for (int i = 0; i < bb.n_scenes; ++i) C_max = max(C_max, bb.sc[i].g.C);
+  const size_t smem = (size_t)kBoxFields * C_max * 32 * kBinWarps * sizeof(float);
+  if (smem + sizeof(uint32_t) * 32 * kBinWarps > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_bin_count_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_bin_count_batch<<<blocks, 32 * kBinWarps, smem, s>>>(bb, dest, counts,
+                                                         reinterpret_cast<BinDesc*>(desc));
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bin_emit_batch(const BatchBins& bb_in, const uint32_t* order, const uint32_t* counts,
+                                  const uint32_t* offsets, uint32_t* keys32, uint32_t* vals,
+                                  const void* desc, const unsigned long long* P_dev,
+                                  unsigned long long P_cap, uint32_t* err, cudaStream_t s) {
+  BatchBins bb = bb_in;
+  const uint32_t blocks = place_blocks(bb, 32 * kEmitWarps);
+  if (blocks == 0) return cudaSuccess;
+  k_bin_emit_batch<<<blocks, 32 * kEmitWarps, 0, s>>>(bb, order, counts, offsets, keys32, vals,
+                                                      reinterpret_cast<const BinDesc*>(desc), P_dev,
+                                                      P_cap, err);
   note_launches(1);
   return cudaGetLastError();
 }

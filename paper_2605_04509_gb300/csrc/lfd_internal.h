@@ -95,6 +95,33 @@ cudaError_t launch_bin_emit_coop(const PanelGeom& g, int64_t M, const float* mea
                                  uint64_t* keys64, uint32_t* vals, const void* desc,
                                  const unsigned long long* P_dev, unsigned long long P_cap,
                                  uint32_t* err, cudaStream_t s);
+// Batched key generation: the scenes' items side by side in the batch arrays
+// (scene s at positions [off, off + n)), one launch per pass for all scenes.
+// A launch gives each scene whole blocks from blk_off on (filled in by the
+// launcher for its block size).
+constexpr int kMaxBinScenes = 16;
+struct SceneBins {
+  PanelGeom g;
+  int64_t M, n, off;  // Gaussians, items (K M), first batch position
+  const float *means2d, *conic_opacity, *color_tau, *depth;
+  uint32_t blk_off;
+};
+struct BatchBins {
+  SceneBins sc[kMaxBinScenes];
+  int n_scenes;
+};
+cudaError_t launch_item_keys_batch(const BatchBins& bb, uint64_t* keys, uint32_t* vals, cudaStream_t s);
+// per scene: inv[off + perm[p]] = p - off
+cudaError_t launch_invert_batch(const BatchBins& bb, const uint32_t* perm, uint32_t* inv, cudaStream_t s);
+// counts and descriptors of all scenes' items at their emission positions
+cudaError_t launch_bin_count_batch(const BatchBins& bb, const uint32_t* dest, uint32_t* counts, void* desc,
+                                   cudaStream_t s);
+// the 32-bit pair keys and values of all scenes (order: scene-local item
+// indices at batch positions)
+cudaError_t launch_bin_emit_batch(const BatchBins& bb, const uint32_t* order, const uint32_t* counts,
+                                  const uint32_t* offsets, uint32_t* keys32, uint32_t* vals,
+                                  const void* desc, const unsigned long long* P_dev,
+                                  unsigned long long P_cap, uint32_t* err, cudaStream_t s);
 // dst[s] = src[idx[s]]
 cudaError_t launch_gather_u32(const uint32_t* src, const uint32_t* idx, int64_t n, uint32_t* dst,
                               cudaStream_t s);
