@@ -460,7 +460,6 @@ __device__ __forceinline__ void bin_emit_block(
   constexpr bool kWide = sizeof(KeyT) == 8;
   __shared__ KeyT s_key[kEmitWarps][CAP];
   __shared__ uint32_t s_val[kEmitWarps][CAP];
-  __shared__ __align__(16) unsigned long long s_desc[kEmitWarps][32][kDescRows + 1];
   const int64_t s = blk * (32 * kEmitWarps) + threadIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (P_dev && *P_dev > P_cap) {  // more pairs than the buffers hold: write nothing
@@ -504,48 +503,51 @@ __device__ __forceinline__ void bin_emit_block(
         ++p;
       });
   }
-  // the other items' tile rows are dealt out to the lanes
-  const int units = (in && n && !redo) ? (int)((h >> 32) & 0xffull) : 0;
-  int U;
+  // The other items' tile rows are dealt out to the lanes, 32 units at a
+  // time in (item, row) order. A unit's first list position is its item's
+  // plus the pairs of the item's earlier rows: with R(u) the pairs of all the
+  // warp's units before u (a running scan over the rounds) and Rb_j those of
+  // item j's first unit (a scan of the counts over the lanes), it is
+  // pos_j + R(u) - Rb_j.
+  const bool units_here = in && n && !redo;
+  const int units = units_here ? (int)((h >> 32) & 0xffull) : 0;
+  int U, NU;
   const int ubase = warp_exclusive(units, lane, &U);
-  // the row masks of the warp's items, fetched into shared memory with
-  // independent 16-byte loads (8 lanes per item, only the rows in use)
-  for (int it = 0; it < 8; ++it) {
-    const int j = it * 4 + (lane >> 3);
-    const int part = lane & 7;  // 16-byte part: words 2 part, 2 part + 1
-    const int uj = __shfl_sync(0xffffffffu, units, j);
-    if (uj > 0 && 2 * part <= uj) {
-      const uint4 w = reinterpret_cast<const uint4*>(desc + (s - lane + j))[part];
-      reinterpret_cast<uint4*>(&s_desc[warp][j][0])[part] = w;
-    }
-  }
-  __syncwarp();
+  const uint32_t rbase = (uint32_t)warp_exclusive(units_here ? (int)n : 0, lane, &NU);
+  // this lane's item: cluster, Gaussian, and the depth half of a 64-bit key
+  const uint32_t k_l = in ? r / (uint32_t)M : 0u;  // K M < 2^32
+  const uint32_t i_l = in ? (uint32_t)(r - (uint64_t)k_l * M) : 0u;
+  const uint32_t d_l = (kWide && units_here) ? __float_as_uint(depth[r]) : 0u;
+  const int64_t s0w = s - lane;  // the warp's first item
+  uint32_t carry = 0;
   for (int b = 0; b < U; b += 32) {
     const int u = b + lane;
     const int j = unit_owner(ubase, u);
     const int rr = u - __shfl_sync(0xffffffffu, ubase, j);
-    const uint32_t rj = __shfl_sync(0xffffffffu, r, j);
-    const uint32_t pj = __shfl_sync(0xffffffffu, pos, j);
-    const unsigned long long hj =
-        ((unsigned long long)__shfl_sync(0xffffffffu, (uint32_t)(h >> 32), j) << 32) |
-        __shfl_sync(0xffffffffu, (uint32_t)h, j);
-    if (u < U) {
-      const int ty0 = (int)(hj & 0xffffull), c0 = (int)((hj >> 16) & 0xffffull);
-      const uint32_t k = rj / (uint32_t)M;
-      const uint32_t i = (uint32_t)(rj - (uint64_t)k * M);
-      const uint64_t lo = kWide ? (((uint64_t)k << 32) | __float_as_uint(depth[rj])) : 0ull;
-      uint32_t p = pj - shift_out;
-      const unsigned long long* dm = &s_desc[warp][j][1];
-      for (int x = 0; x < rr; ++x) p += (uint32_t)__popcll(dm[x]);
-      unsigned long long mask = dm[rr];
-      while (mask) {
-        const int bit = __ffsll((long long)mask) - 1;
-        mask &= mask - 1ull;
-        const uint32_t t = (uint32_t)((ty0 + rr) * g.TX + c0 + bit);
-        kdst[p] = kWide ? (KeyT)(((uint64_t)t << shift) | lo) : (KeyT)((t << shift) | g.key_code | k);
-        vdst[p] = i;
-        ++p;
-      }
+    const unsigned long long hj = __shfl_sync(0xffffffffu, h, j);
+    const unsigned long long mask = u < U ? desc[s0w + j].mask[rr] : 0ull;
+    const uint32_t c = (uint32_t)__popcll(mask);
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    uint32_t p = __shfl_sync(0xffffffffu, pos, j) - shift_out + carry + (incl - c) -
+                 __shfl_sync(0xffffffffu, rbase, j);
+    carry += __shfl_sync(0xffffffffu, incl, 31);
+    const uint32_t k = __shfl_sync(0xffffffffu, k_l, j);
+    const uint32_t i = __shfl_sync(0xffffffffu, i_l, j);
+    const uint64_t lo = kWide ? (((uint64_t)k << 32) | __shfl_sync(0xffffffffu, d_l, j)) : 0ull;
+    const int ty0 = (int)(hj & 0xffffull), c0 = (int)((hj >> 16) & 0xffffull);
+    unsigned long long m = mask;
+    while (m) {
+      const int bit = __ffsll((long long)m) - 1;
+      m &= m - 1ull;
+      const uint32_t t = (uint32_t)((ty0 + rr) * g.TX + c0 + bit);
+      kdst[p] = kWide ? (KeyT)(((uint64_t)t << shift) | lo) : (KeyT)((t << shift) | g.key_code | k);
+      vdst[p] = i;
+      ++p;
     }
   }
   if (staged) {
