@@ -306,7 +306,7 @@ LFD_API int lfd_plan_copy_lists(const lfd_plan *plan, uint32_t *list, uint32_t *
  * from a CUDA graph use capacity mode (lfd_plan_reserve) instead.
  * Same arguments, stages and results (bit for bit) as lfd_render_projected;
  * the plan must have been created beforehand. All scratch memory comes from
- * one fixed array of about 4.4 MB inside the library (every GPU that loads
+ * one fixed array of about 4.9 MB inside the library (every GPU that loads
  * the library holds it until the process exits), which bounds the frame:
  * K * M <= 32768 projected items, T * K <= 16384 (tile, cluster) lists and
  * P <= 131072 Gaussian-tile pairs; larger frames return LFD_ERR_CAPACITY

@@ -30,8 +30,8 @@ constexpr size_t kOffPairVal = kOffPairKey + align256(2 * kNaPairs * 8);      //
 constexpr size_t kOffRanges = kOffPairVal + align256(2 * kNaPairs * 4);       // uint2[ranges]
 constexpr size_t kOffSmall = kOffRanges + align256(kNaRanges * 8);            // u64[4]
 constexpr size_t kOffRadix = kOffSmall + 256;                                 // sort / scan temp
-constexpr size_t kRadixBytes = 256 * 1024;
-constexpr size_t kScratchBytes = kOffRadix + kRadixBytes;  // about 4.4 MB
+constexpr size_t kRadixBytes = 512 * 1024;
+constexpr size_t kScratchBytes = kOffRadix + kRadixBytes;  // about 4.9 MB
 
 // The scratch array. Every GPU that loads the library holds it until the
 // process exits. All calls share it: concurrent calls race.

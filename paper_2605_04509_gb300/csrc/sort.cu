@@ -132,11 +132,24 @@ struct RadixOf {
   static constexpr int radix = 1 << bits;
 };
 constexpr int kMaxRadix = 512;
-constexpr int kSortThreads = 512;
-constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortRounds = 8;
-constexpr int kSortTile = kSortThreads * kSortRounds;  // 4096 items
-static_assert(kSortThreads >= kMaxRadix, "one thread per digit in the digit phases");
+// Block shape per key type: threads, and rounds of 32 items per warp; a
+// tile is threads x rounds items. The 64-bit keys (the item sort, a few
+// million items) take 2048-item tiles: the scatter's double buffer then
+// needs 72 KB instead of 144 KB and three blocks fit an SM instead of one
+// (key generation 2.00 -> 1.97 ms per paper4k frame). For the 32-bit pair
+// keys, 8192-item tiles of 1024 threads (longer digit runs, one block per
+// SM) made the sort stage slower (1.74 against 1.42 ms).
+template <typename K>
+struct SortCfg {
+  static constexpr int threads = 512;
+  static constexpr int warps = threads / 32;
+  static constexpr int rounds = sizeof(K) == 8 ? 4 : 8;
+  static constexpr int tile = threads * rounds;
+  static_assert(threads >= RadixOf<K>::radix, "one thread per digit in the digit phases");
+};
+// the smallest tile of any key type (sizes the digit tables)
+constexpr int kMinSortTile =
+    SortCfg<uint32_t>::tile < SortCfg<uint64_t>::tile ? SortCfg<uint32_t>::tile : SortCfg<uint64_t>::tile;
 
 template <typename K>
 __device__ __forceinline__ int digit_of(K key, int shift, int mask) {
@@ -154,10 +167,12 @@ __device__ __forceinline__ int64_t live_count(int64_t n_cap, const unsigned long
 // apart and their shared-memory increments rarely collide; each warp counts
 // into its own histogram. Tiles past the live count write zeros.
 template <typename K>
-__global__ void __launch_bounds__(kSortThreads)
+__global__ void __launch_bounds__(SortCfg<K>::threads)
     k_rts_hist(const K* __restrict__ keys, int64_t n_cap, const unsigned long long* __restrict__ n_dev,
                int shift, int mask, uint32_t* __restrict__ hist, int64_t nb) {
   constexpr int kRadix = RadixOf<K>::radix;
+  constexpr int kSortThreads = SortCfg<K>::threads, kSortWarps = SortCfg<K>::warps;
+  constexpr int kSortRounds = SortCfg<K>::rounds, kSortTile = SortCfg<K>::tile;
   __shared__ uint32_t s_h[kSortWarps][kRadix];
   const int warp = threadIdx.x >> 5;
   for (int a = threadIdx.x; a < kSortWarps * kRadix; a += kSortThreads) (&s_h[0][0])[a] = 0;
@@ -209,12 +224,14 @@ __device__ __forceinline__ unsigned digit_peers(int d, bool valid) {
 // Stable scatter of one pass. Block b handles tiles b, b + G, b + 2G, ...
 // (G = gridDim.x); tile t's output base per digit is hscan[d * nb + t].
 template <typename K>
-__global__ void __launch_bounds__(kSortThreads)
+__global__ void __launch_bounds__(SortCfg<K>::threads)
     k_rts_scatter(const K* __restrict__ kin, K* __restrict__ kout, const uint32_t* __restrict__ vin,
                   uint32_t* __restrict__ vout, int64_t n_cap, const unsigned long long* __restrict__ n_dev,
                   int shift, int mask, const uint32_t* __restrict__ hscan, int64_t nb,
                   uint32_t* __restrict__ err) {
   constexpr int kRadix = RadixOf<K>::radix;
+  constexpr int kSortThreads = SortCfg<K>::threads, kSortWarps = SortCfg<K>::warps;
+  constexpr int kSortRounds = SortCfg<K>::rounds, kSortTile = SortCfg<K>::tile;
   extern __shared__ __align__(128) unsigned char s_raw[];
   // [in0 keys][in0 vals][in1 keys][in1 vals][out keys][out vals]
   constexpr size_t kBuf = (size_t)kSortTile * (sizeof(K) + sizeof(uint32_t));
@@ -354,7 +371,7 @@ __global__ void __launch_bounds__(kSortThreads)
 
 template <typename K>
 constexpr size_t scatter_smem() {
-  return (size_t)kSortTile * (sizeof(K) + sizeof(uint32_t)) * 3;
+  return (size_t)SortCfg<K>::tile * (sizeof(K) + sizeof(uint32_t)) * 3;
 }
 
 // resident blocks of the scatter kernel (its persistent grid)
@@ -363,7 +380,7 @@ int scatter_grid(int64_t tiles) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rts_scatter<K>, kSortThreads,
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rts_scatter<K>, SortCfg<K>::threads,
                                                 scatter_smem<K>());
   const int64_t g = (int64_t)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
   return (int)(g < tiles ? g : (tiles > 0 ? tiles : 1));
@@ -375,6 +392,7 @@ cudaError_t radix_sort_impl(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals
                             bool* result_in_alt, uint32_t* err, cudaStream_t s) {
   *result_in_alt = false;
   if (n_cap <= 1 || end_bit <= begin_bit) return cudaSuccess;
+  constexpr int kSortThreads = SortCfg<K>::threads, kSortTile = SortCfg<K>::tile;
   const int64_t nb = (n_cap + kSortTile - 1) / kSortTile;
   constexpr int kRadix = RadixOf<K>::radix;
   uint32_t* hist = reinterpret_cast<uint32_t*>(temp);
@@ -450,7 +468,7 @@ cudaError_t scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, void* t
 }
 
 size_t radix_temp_bytes(int64_t n) {
-  const int64_t nb = (n + kSortTile - 1) / kSortTile;
+  const int64_t nb = (n + kMinSortTile - 1) / kMinSortTile;
   return (size_t)nb * kMaxRadix * 2 * sizeof(uint32_t) + scan_temp_bytes(nb * kMaxRadix) +
          sizeof(unsigned long long) + 256;
 }
