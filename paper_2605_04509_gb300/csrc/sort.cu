@@ -2,7 +2,8 @@
 // the Gaussian-tile pairs are sorted so that every (tile, cluster) list is
 // contiguous and depth-ordered; Alg. 1 stage 3).
 //
-// Radix sort: reduce-then-scan per digit (8 or 9 bits). Pass = (1) per-tile digit
+// Radix sort: reduce-then-scan per digit (at most 8 bits for 32-bit keys, 9 for
+// 64-bit keys). Pass = (1) per-tile digit
 // histogram into a digit-major table, (2) exclusive scan of that table, which
 // yields every tile's global output base per digit, (3) stable scatter. The
 // scatter kernel is persistent: each block walks its share of the tiles and,
@@ -241,7 +242,7 @@ __global__ void __launch_bounds__(SortCfg<K>::threads)
   };
   K* s_key = reinterpret_cast<K*>(s_raw + 2 * kBuf);
   uint32_t* s_val = reinterpret_cast<uint32_t*>(s_key + kSortTile);
-  // per-warp digit counters (at most 4096 per tile: 16 bits suffice)
+  // per-warp digit counters (at most 4096 items per tile: 16 bits suffice)
   __shared__ uint16_t s_wcnt[kSortWarps][kRadix];
   __shared__ uint32_t s_base[kRadix];
   __shared__ uint32_t s_dstart[kRadix];
