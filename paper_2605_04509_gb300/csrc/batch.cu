@@ -206,8 +206,8 @@ int lfd_batch_reserve(lfd_batch* b, const int64_t* max_gaussians, int64_t max_pa
   B_CUDA(b->offsets.ensure(items4));
   B_CUDA(b->scan_tmp.ensure(scan_temp_bytes(items + 1)));
   B_CUDA(b->bin_desc.ensure((size_t)(items + 1) * kBinDescBytes));
-  const size_t st = radix_temp_bytes(items) > radix_temp_bytes(max_pairs) ? radix_temp_bytes(items)
-                                                                         : radix_temp_bytes(max_pairs);
+  const size_t st = radix_temp_bytes(items, 8) > radix_temp_bytes(max_pairs, 4) ? radix_temp_bytes(items, 8)
+                                                                               : radix_temp_bytes(max_pairs, 4);
   B_CUDA(b->radix_tmp.ensure(st));
   B_CUDA(b->ranges.ensure((size_t)b->n * b->T_max * b->K_glob * sizeof(uint2)));
   b->cap_items = items;

@@ -627,7 +627,7 @@ static int render_projected_impl(lfd_plan* p, int64_t M, const float* means2d,
       if ((rc = p->item_key[b].ensure((size_t)(n_items + 1) * 8)) != LFD_OK) return rc;
       if ((rc = p->item_val[b].ensure((size_t)(n_items + 1) * 4)) != LFD_OK) return rc;
     }
-    if ((rc = p->radix_tmp.ensure(radix_temp_bytes(n_items))) != LFD_OK) return rc;
+    if ((rc = p->radix_tmp.ensure(radix_temp_bytes(n_items, 8))) != LFD_OK) return rc;
     LFD_CUDA(launch_item_keys(g, M, depth, color_tau, p->item_key[0].as<uint64_t>(),
                               p->item_val[0].as<uint32_t>(), s));
     bool alt = false;
@@ -666,7 +666,7 @@ static int render_projected_impl(lfd_plan* p, int64_t M, const float* means2d,
     if ((rc = p->pair_key[b].ensure((size_t)(P + 1) * kbytes)) != LFD_OK) return rc;
     if ((rc = p->pair_val[b].ensure((size_t)(P + 1) * 4)) != LFD_OK) return rc;
   }
-  if ((rc = p->radix_tmp.ensure(radix_temp_bytes((int64_t)P))) != LFD_OK) return rc;
+  if ((rc = p->radix_tmp.ensure(radix_temp_bytes((int64_t)P, (int)kbytes))) != LFD_OK) return rc;
   if ((rc = p->ranges.ensure((size_t)g.T * g.K * sizeof(uint2))) != LFD_OK) return rc;
   LFD_CUDA(launch_bin_emit_coop(g, M, means2d, conic_opacity, color_tau, depth, order, n_items,
                                 p->counts.as<uint32_t>(), p->offsets.as<uint32_t>(),
@@ -1032,8 +1032,10 @@ int lfd_plan_reserve(lfd_plan* p, int64_t max_gaussians, int64_t max_pairs) {
   const int64_t n = (int64_t)g.K * max_gaussians;
   int rc;
   const size_t items4 = (size_t)(n + 1) * 4;
-  const size_t sort_tmp = radix_temp_bytes(n) > radix_temp_bytes(max_pairs) ? radix_temp_bytes(n)
-                                                                            : radix_temp_bytes(max_pairs);
+  const int pair_key_bytes = p->opts.sort_mode == LFD_SORT_KEY64 ? 8 : 4;
+  const size_t sort_tmp = radix_temp_bytes(n, 8) > radix_temp_bytes(max_pairs, pair_key_bytes)
+                              ? radix_temp_bytes(n, 8)
+                              : radix_temp_bytes(max_pairs, pair_key_bytes);
   if ((rc = p->proj_means.ensure((size_t)(n * g.C + 1) * 8)) != LFD_OK ||
       (rc = p->proj_co.ensure((size_t)(n + 1) * 16)) != LFD_OK ||
       (rc = p->proj_ct.ensure((size_t)(n + 1) * 16)) != LFD_OK ||

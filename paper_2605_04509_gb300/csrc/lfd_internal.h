@@ -148,8 +148,9 @@ size_t scan_temp_bytes(int64_t n);
 // exclusive scan of n uint32 into out; the 64-bit total goes to *total_dev
 cudaError_t scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, void* temp,
                            unsigned long long* total_dev, cudaStream_t s);
-// bytes of sort scratch for up to n items (n the capacity)
-size_t radix_temp_bytes(int64_t n);
+// bytes of sort scratch for up to n items (n the capacity) with keys of
+// key_bytes (4 or 8) bytes
+size_t radix_temp_bytes(int64_t n, int key_bytes);
 // Stable LSD radix sort of (key, value) by key bits [begin_bit, end_bit);
 // ping-pongs between the two buffers; *result_in_alt tells where the result
 // ends up (it depends on the bit range only). n is a host-side capacity;

@@ -113,7 +113,7 @@ extern "C" int lfd_render_projected_noalloc(lfd_plan* plan, int64_t M, const flo
   unsigned long long* d_small = reinterpret_cast<unsigned long long*>(sb + kOffSmall);
   uint32_t* d_err = reinterpret_cast<uint32_t*>(d_small + 3);  // zero at load
   void* temp = sb + kOffRadix;
-  if (radix_temp_bytes(kNaPairs) > kRadixBytes || radix_temp_bytes(kNaItems) > kRadixBytes ||
+  if (radix_temp_bytes(kNaPairs, 8) > kRadixBytes || radix_temp_bytes(kNaItems, 8) > kRadixBytes ||
       scan_temp_bytes(kNaItems + 1) > kRadixBytes)
     return na_fail(LFD_ERR_CAPACITY, "scratch layout too small");
 

@@ -148,9 +148,6 @@ struct SortCfg {
   static constexpr int tile = threads * rounds;
   static_assert(threads >= RadixOf<K>::radix, "one thread per digit in the digit phases");
 };
-// the smallest tile of any key type (sizes the digit tables)
-constexpr int kMinSortTile =
-    SortCfg<uint32_t>::tile < SortCfg<uint64_t>::tile ? SortCfg<uint32_t>::tile : SortCfg<uint64_t>::tile;
 
 template <typename K>
 __device__ __forceinline__ int digit_of(K key, int shift, int mask) {
@@ -468,10 +465,15 @@ cudaError_t scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, void* t
   return cudaGetLastError();
 }
 
-size_t radix_temp_bytes(int64_t n) {
-  const int64_t nb = (n + kMinSortTile - 1) / kMinSortTile;
-  return (size_t)nb * kMaxRadix * 2 * sizeof(uint32_t) + scan_temp_bytes(nb * kMaxRadix) +
-         sizeof(unsigned long long) + 256;
+template <typename K>
+size_t radix_temp_bytes_of(int64_t n) {
+  const int64_t nb = (n + SortCfg<K>::tile - 1) / SortCfg<K>::tile;
+  const int64_t cells = nb * RadixOf<K>::radix;
+  return (size_t)cells * 2 * sizeof(uint32_t) + scan_temp_bytes(cells) + sizeof(unsigned long long) + 256;
+}
+
+size_t radix_temp_bytes(int64_t n, int key_bytes) {
+  return key_bytes == 8 ? radix_temp_bytes_of<uint64_t>(n) : radix_temp_bytes_of<uint32_t>(n);
 }
 
 cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals,
