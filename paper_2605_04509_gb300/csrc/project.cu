@@ -1,6 +1,8 @@
 // Projection with cross-view coherent attribute reuse (Sec. 4.2, Eq. 5-6;
-// Alg. 1 stage 1). One thread per Gaussian: the 3D covariance and the SH
-// coefficients are loaded once, then for every cluster k the representative
+// Alg. 1 stage 1). One thread per Gaussian: the 3D covariance is built once
+// and the block's SH records are staged in shared memory (coalesced loads,
+// widened to FP32; a record per thread at a stride of 49 words, so the lanes
+// reading one coefficient hit 32 different banks), then for every cluster k the representative
 // view gives the 2D covariance (EWA splatting with the 3DGS Jacobian clamp and
 // +0.3 low-pass), its inverse (conic), the depth and the SH colour, and every
 // slot view of the cluster gives a 2D mean (Eq. 5). FP32 throughout.
@@ -49,14 +51,46 @@ __device__ __forceinline__ float depth_rn(const float* c, float x, float y, floa
                    c[11]);
 }
 
+constexpr int kProjThreads = 128;
+constexpr int kShStride = 49;  // words per staged SH record (48 values, padded)
+
 template <typename A>
-__global__ void __launch_bounds__(128) k_project(PanelGeom g, CamTable cams, ProjectArgs a) {
-  const int64_t i = a.m_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.m_end) return;
+__global__ void __launch_bounds__(kProjThreads) k_project(PanelGeom g, CamTable cams, ProjectArgs a) {
+  __shared__ float s_sh[kProjThreads * kShStride];
+  const int64_t b0 = a.m_begin + (int64_t)blockIdx.x * kProjThreads;  // the block's first Gaussian
+  const int64_t i = b0 + threadIdx.x;
   const A* quats = reinterpret_cast<const A*>(a.quats);
   const A* scales = reinterpret_cast<const A*>(a.scales);
   const A* opac = reinterpret_cast<const A*>(a.opac);
   const A* shs = reinterpret_cast<const A*>(a.sh);
+  {
+    // the block's SH records into shared memory, zeros past the degree
+    const int nb = (int)min((int64_t)kProjThreads, a.m_end - b0);
+    const int ncoef = (a.sh_degree + 1) * (a.sh_degree + 1);
+    const int nv = ncoef * 3;
+    constexpr int kPerVec = 16 / (int)sizeof(A);
+    if (ncoef == 16 && (reinterpret_cast<uintptr_t>(shs) & 15) == 0) {
+      // degree 3: the records are one contiguous run of 48 nb values
+      const uint4* src = reinterpret_cast<const uint4*>(shs + (size_t)b0 * 48);
+      for (int v = threadIdx.x; v < nb * 48 / kPerVec; v += kProjThreads) {
+        const uint4 w = src[v];
+        const A* e = reinterpret_cast<const A*>(&w);
+#pragma unroll
+        for (int q = 0; q < kPerVec; ++q) {
+          const int f = v * kPerVec + q;  // value f of the run: record f / 48
+          s_sh[(f / 48) * kShStride + f % 48] = to_f32(e[q]);
+        }
+      }
+    } else {
+      for (int f = threadIdx.x; f < nb * 48; f += kProjThreads) {
+        const int r = f / 48, c = f % 48;
+        s_sh[r * kShStride + c] = c < nv ? to_f32(shs[((size_t)b0 + r) * nv + c]) : 0.f;
+      }
+    }
+  }
+  __syncthreads();
+  if (i >= a.m_end) return;
+  const float* sh = s_sh + threadIdx.x * kShStride;  // sh[3 c + u]
   const float mx = a.means[3 * i], my = a.means[3 * i + 1], mz = a.means[3 * i + 2];
   const float4 q4 = make_float4(to_f32(quats[4 * i]), to_f32(quats[4 * i + 1]), to_f32(quats[4 * i + 2]),
                                 to_f32(quats[4 * i + 3]));
@@ -80,27 +114,6 @@ __global__ void __launch_bounds__(128) k_project(PanelGeom g, CamTable cams, Pro
   const float S12 = r10 * r20 * s0 + r11 * r21 * s1 + r12 * r22 * s2;
   const float S22 = r20 * r20 * s0 + r21 * r21 * s1 + r22 * r22 * s2;
 
-  const int ncoef = (a.sh_degree + 1) * (a.sh_degree + 1);
-  float sh[16][3];
-  constexpr int kShVec = 48 * (int)sizeof(A) / 16;  // 16-byte loads of a degree-3 record
-  if (ncoef == 16 && (reinterpret_cast<uintptr_t>(shs) & 15) == 0) {
-    // degree 3: the record (48 values, a multiple of 16 bytes) in 16-byte loads
-    A raw[48];
-    const uint4* src = reinterpret_cast<const uint4*>(shs + (size_t)i * 48);
-#pragma unroll
-    for (int v = 0; v < kShVec; ++v) reinterpret_cast<uint4*>(raw)[v] = src[v];
-#pragma unroll
-    for (int c = 0; c < 16; ++c)
-#pragma unroll
-      for (int u = 0; u < 3; ++u) sh[c][u] = to_f32(raw[c * 3 + u]);
-  } else {
-#pragma unroll
-    for (int c = 0; c < 16; ++c) {
-#pragma unroll
-      for (int u = 0; u < 3; ++u)
-        sh[c][u] = c < ncoef ? to_f32(shs[((size_t)i * ncoef + c) * 3 + u]) : 0.f;
-    }
-  }
   const bool opaque_enough = (double)o >= 1.0 / 255.0;
   const float tau_i = 2.f * logf(255.f * o);
   const float nanf_ = __int_as_float(0x7fc00000);
@@ -175,7 +188,7 @@ __global__ void __launch_bounds__(128) k_project(PanelGeom g, CamTable cams, Pro
         for (int u = 0; u < 3; ++u) {
           float acc = 0.f;
 #pragma unroll
-          for (int c = 0; c < 16; ++c) acc += b[c] * sh[c][u];
+          for (int c = 0; c < 16; ++c) acc += b[c] * sh[3 * c + u];
           rgb[u] = fmaxf(acc + 0.5f, 0.f);
         }
         ct = make_float4(rgb[0], rgb[1], rgb[2], tau_i);
@@ -217,7 +230,7 @@ cudaError_t launch_project(const PanelGeom& g, const CamTable& cams, const Proje
   if (a.m_end < 0 || a.m_end > a.M) a.m_end = a.M;
   if (a.m_begin < 0) a.m_begin = 0;
   if (a.m_end <= a.m_begin) return cudaSuccess;
-  const int threads = 128;
+  const int threads = kProjThreads;
   const int64_t blocks = (a.m_end - a.m_begin + threads - 1) / threads;
   if (a.attr_dtype == LFD_DTYPE_F16)
     k_project<__half><<<(unsigned)blocks, threads, 0, s>>>(g, cams, a);
