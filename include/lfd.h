@@ -263,9 +263,8 @@ LFD_API int lfd_render_fullframe(lfd_plan *plan, const lfd_gaussians *g, const l
  * image back and returns once it is in out_rgb (or, on an error, once every
  * copy it queued has finished). The copies run on plan-owned upload and
  * download streams: the Gaussians go up in four chunks, each projected as it
- * lands, and the remapped blend runs in four bands of tile rows on
- * plan-owned streams forked from `stream`, each band's rows copied back as
- * soon as the band is done. The image equals lfd_render's bit for bit. It is
+ * lands, and the image goes back once the blend is done. The image equals
+ * lfd_render's bit for bit. It is
  * lfd_render_host_async followed by lfd_render_host_wait. */
 LFD_API int lfd_render_host(lfd_plan *plan, const lfd_gaussians *g_host,
                     const lfd_camera *cams, int32_t num_cams, float *out_rgb_host,

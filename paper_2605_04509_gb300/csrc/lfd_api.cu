@@ -84,15 +84,15 @@ bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 namespace {
 // Transfers of lfd_render_host(_async), overlapped with the kernels: the
 // Gaussians go up in kHostChunks chunks on an upload stream and each chunk is
-// projected as soon as it has landed; the remapped blend runs in kHostBands
-// bands of tile rows, launched on streams of their own so that each band's
-// last blocks share the GPU with the next band's first ones, and each band's
-// image rows go back on a download stream as soon as the band is done. The
-// device copies of the inputs and the device image are double-buffered
-// (parity of the frame), so a frame's upload can run under the previous
-// frame's blend.
+// projected as soon as it has landed; the image goes back on a download
+// stream once the blend is done. The device copies of the inputs and the
+// device image are double-buffered (parity of the frame), so a frame's upload
+// runs under the previous frame's blend and its download under the next
+// frame's first stages. (Blending in four bands of tile rows on forked
+// streams, each band's rows going back as soon as it was done, was slower:
+// every band's launch has its own tail; 109.5 against 114.3 frames/s
+// pipelined and 98.4 against 98.8 synchronous on paper4k.)
 constexpr int kHostChunks = 4;
-constexpr int kHostBands = 4;
 struct HostIO {
   const void* src[5];   // host attribute arrays
   void* dst[5];         // their device copies
@@ -102,10 +102,8 @@ struct HostIO {
 };
 struct HostPipe {
   cudaStream_t up = nullptr, down = nullptr;  // upload, download
-  cudaStream_t band[kHostBands] = {};
   cudaEvent_t chunk[kHostChunks] = {};
-  cudaEvent_t band_done[kHostBands] = {};
-  cudaEvent_t fork = nullptr;
+  cudaEvent_t blend_done = nullptr;
   cudaEvent_t inputs_free[2] = {};  // the projection that read input buffer f ended
   cudaEvent_t image_free[2] = {};   // the download of device image f ended
   int frame = 0;                    // frames queued so far
@@ -324,15 +322,11 @@ void lfd_plan_destroy(lfd_plan* p) {
   if (io.down) cudaStreamSynchronize(io.down);
   for (cudaEvent_t e : io.chunk)
     if (e) cudaEventDestroy(e);
-  for (cudaEvent_t e : io.band_done)
-    if (e) cudaEventDestroy(e);
+  if (io.blend_done) cudaEventDestroy(io.blend_done);
   for (int f = 0; f < 2; ++f) {
     if (io.inputs_free[f]) cudaEventDestroy(io.inputs_free[f]);
     if (io.image_free[f]) cudaEventDestroy(io.image_free[f]);
   }
-  if (io.fork) cudaEventDestroy(io.fork);
-  for (cudaStream_t b : io.band)
-    if (b) cudaStreamDestroy(b);
   if (io.up) cudaStreamDestroy(io.up);
   if (io.down) cudaStreamDestroy(io.down);
   delete p;
@@ -583,7 +577,7 @@ int lfd_project(lfd_plan* p, const lfd_gaussians* gs, const lfd_camera* cams, in
 }
 
 // Stages 2-4 from projected attributes. With io, the image also goes back to
-// io->out_host on the transfer stream (band by band for the remapped blend).
+// io->out_host on the download stream.
 static int render_projected_impl(lfd_plan* p, int64_t M, const float* means2d,
                                  const float* conic_opacity, const float* color_tau,
                                  const float* depth, float* out_rgb, void* stream, lfd_stats* stats,
@@ -717,50 +711,18 @@ static int render_projected_impl(lfd_plan* p, int64_t M, const float* means2d,
   const bool kept = (p->flags & LFD_FLAG_KEEP_BLEND_STATE) && p->opts.remap && !p->fullframe;
   ba.keep = kept ? p->keep.as<uint2>() : nullptr;
   const size_t row_floats = (size_t)g.W * 3;
-  if (p->opts.remap && !p->fullframe && io) {
-    // bands of tile rows, forked from s and joined back into it; the device
-    // image is written once the download of its previous frame has ended
+  // the device image is written once the download of its previous frame has ended
+  if (io) LFD_CUDA(cudaStreamWaitEvent(s, p->io.image_free[io->parity], 0));
+  if (p->fullframe)
+    LFD_CUDA(launch_blend_fullframe(g, ba, s));
+  else if (p->opts.remap)
+    LFD_CUDA(launch_blend(g, ba, s));
+  else
+    LFD_CUDA(launch_blend_raster(g, ba, s));
+  if (io) {
     HostPipe& hp = p->io;
-    LFD_CUDA(cudaStreamWaitEvent(s, hp.image_free[io->parity], 0));
-    LFD_CUDA(cudaEventRecord(hp.fork, s));
-    int done = 0;
-    for (int b = 0; b < kHostBands; ++b) {
-      const int ty0 = done, ty1 = g.TY * (b + 1) / kHostBands;
-      cudaStream_t sb = hp.band[b];
-      cudaEvent_t ev_b = hp.band_done[b];
-      LFD_CUDA(cudaStreamWaitEvent(sb, hp.fork, 0));
-      if (ty1 > ty0) {
-        done = ty1;
-        ba.t_begin = ty0 * g.TX;
-        ba.t_end = ty1 * g.TX;
-        LFD_CUDA(launch_blend(g, ba, sb));
-      }
-      LFD_CUDA(cudaEventRecord(ev_b, sb));
-      LFD_CUDA(cudaStreamWaitEvent(s, ev_b, 0));
-      if (ty1 > ty0) {
-        const int y0 = ty0 * g.TH, y1 = min(ty1 * g.TH, g.H);
-        LFD_CUDA(cudaStreamWaitEvent(hp.down, ev_b, 0));
-        LFD_CUDA(cudaMemcpyAsync(io->out_host + (size_t)y0 * row_floats, out_rgb + (size_t)y0 * row_floats,
-                                 (size_t)(y1 - y0) * row_floats * sizeof(float), cudaMemcpyDeviceToHost,
-                                 hp.down));
-      }
-    }
-    LFD_CUDA(cudaEventRecord(hp.image_free[io->parity], hp.down));
-    ba.t_begin = 0;
-    ba.t_end = -1;
-  } else {
-    if (io) LFD_CUDA(cudaStreamWaitEvent(s, p->io.image_free[io->parity], 0));
-    if (p->fullframe)
-      LFD_CUDA(launch_blend_fullframe(g, ba, s));
-    else if (p->opts.remap)
-      LFD_CUDA(launch_blend(g, ba, s));
-    else
-      LFD_CUDA(launch_blend_raster(g, ba, s));
-  }
-  if (io && (p->fullframe || !p->opts.remap)) {
-    HostPipe& hp = p->io;
-    LFD_CUDA(cudaEventRecord(hp.band_done[0], s));
-    LFD_CUDA(cudaStreamWaitEvent(hp.down, hp.band_done[0], 0));
+    LFD_CUDA(cudaEventRecord(hp.blend_done, s));
+    LFD_CUDA(cudaStreamWaitEvent(hp.down, hp.blend_done, 0));
     LFD_CUDA(cudaMemcpyAsync(io->out_host, out_rgb, (size_t)g.H * row_floats * sizeof(float),
                              cudaMemcpyDeviceToHost, hp.down));
     LFD_CUDA(cudaEventRecord(hp.image_free[io->parity], hp.down));
@@ -937,15 +899,12 @@ int lfd_render_fullframe(lfd_plan* p, const lfd_gaussians* gs, const lfd_camera*
 }
 
 static int create_host_pipe(HostPipe& hp) {
-  for (cudaStream_t& b : hp.band)
-    if (!b) LFD_CUDA(cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking));
   if (!hp.up) LFD_CUDA(cudaStreamCreateWithFlags(&hp.up, cudaStreamNonBlocking));
   if (!hp.down) LFD_CUDA(cudaStreamCreateWithFlags(&hp.down, cudaStreamNonBlocking));
-  cudaEvent_t* evs[] = {&hp.chunk[0], &hp.chunk[1], &hp.chunk[2], &hp.chunk[3],
-                        &hp.band_done[0], &hp.band_done[1], &hp.band_done[2], &hp.band_done[3],
-                        &hp.fork, &hp.inputs_free[0], &hp.inputs_free[1], &hp.image_free[0],
+  cudaEvent_t* evs[] = {&hp.chunk[0],       &hp.chunk[1],       &hp.chunk[2],      &hp.chunk[3],
+                        &hp.blend_done,     &hp.inputs_free[0], &hp.inputs_free[1], &hp.image_free[0],
                         &hp.image_free[1]};
-  static_assert(kHostChunks == 4 && kHostBands == 4, "event list");
+  static_assert(kHostChunks == 4, "event list");
   for (cudaEvent_t* e : evs)
     if (!*e) LFD_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
   return LFD_OK;
