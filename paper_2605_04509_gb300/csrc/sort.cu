@@ -213,6 +213,55 @@ __global__ void __launch_bounds__(SortCfg<K>::threads)
   }
 }
 
+// Per digit, the exclusive scan of its row of the digit-major table (the
+// tiles' counts of that digit) and the row total: one block per digit. The
+// scatter adds the exclusive scan of the row totals, so a pass needs one scan
+// launch instead of three.
+constexpr int kRowScanThreads = 512;
+constexpr int kRowScanItems = 4;
+
+__global__ void __launch_bounds__(kRowScanThreads)
+    k_rts_rowscan(const uint32_t* __restrict__ hist, uint32_t* __restrict__ hscan, int64_t nb,
+                  uint32_t* __restrict__ rowtot) {
+  __shared__ uint32_t s_w[kRowScanThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t* row = hist + (int64_t)blockIdx.x * nb;
+  uint32_t* out = hscan + (int64_t)blockIdx.x * nb;
+  uint32_t carry = 0;
+  for (int64_t base = 0; base < nb; base += kRowScanThreads * kRowScanItems) {
+    const int64_t i0 = base + (int64_t)threadIdx.x * kRowScanItems;
+    uint32_t v[kRowScanItems];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int q = 0; q < kRowScanItems; ++q) {
+      v[q] = i0 + q < nb ? row[i0 + q] : 0u;
+      sum += v[q];
+    }
+    uint32_t x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    uint32_t pre = 0, all = 0;
+    for (int w = 0; w < kRowScanThreads / 32; ++w) {
+      if (w < warp) pre += s_w[w];
+      all += s_w[w];
+    }
+    uint32_t run = carry + pre + x - sum;
+#pragma unroll
+    for (int q = 0; q < kRowScanItems; ++q) {
+      if (i0 + q < nb) out[i0 + q] = run;
+      run += v[q];
+    }
+    carry += all;
+    __syncthreads();  // s_w is reused by the next chunk
+  }
+  if (threadIdx.x == 0) rowtot[blockIdx.x] = carry;
+}
+
 // Peer mask of the lanes holding the same digit (invalid lanes form a group
 // of their own): one warp match instead of a ballot per digit bit.
 __device__ __forceinline__ unsigned digit_peers(int d, bool valid) {
@@ -220,13 +269,14 @@ __device__ __forceinline__ unsigned digit_peers(int d, bool valid) {
 }
 
 // Stable scatter of one pass. Block b handles tiles b, b + G, b + 2G, ...
-// (G = gridDim.x); tile t's output base per digit is hscan[d * nb + t].
+// (G = gridDim.x); tile t's output base for digit d is the exclusive scan of
+// the row totals at d plus hscan[d * nb + t].
 template <typename K>
 __global__ void __launch_bounds__(SortCfg<K>::threads)
     k_rts_scatter(const K* __restrict__ kin, K* __restrict__ kout, const uint32_t* __restrict__ vin,
                   uint32_t* __restrict__ vout, int64_t n_cap, const unsigned long long* __restrict__ n_dev,
-                  int shift, int mask, const uint32_t* __restrict__ hscan, int64_t nb,
-                  uint32_t* __restrict__ err) {
+                  int shift, int mask, const uint32_t* __restrict__ hscan,
+                  const uint32_t* __restrict__ rowtot, int64_t nb, uint32_t* __restrict__ err) {
   constexpr int kRadix = RadixOf<K>::radix;
   constexpr int kSortThreads = SortCfg<K>::threads, kSortWarps = SortCfg<K>::warps;
   constexpr int kSortRounds = SortCfg<K>::rounds, kSortTile = SortCfg<K>::tile;
@@ -242,6 +292,7 @@ __global__ void __launch_bounds__(SortCfg<K>::threads)
   // per-warp digit counters (at most 4096 items per tile: 16 bits suffice)
   __shared__ uint16_t s_wcnt[kSortWarps][kRadix];
   __shared__ uint32_t s_base[kRadix];
+  __shared__ uint32_t s_dbase[kRadix];
   __shared__ uint32_t s_dstart[kRadix];
   __shared__ uint32_t s_wsum[kRadix / 32];
   __shared__ __align__(8) unsigned long long s_bar[2];
@@ -255,6 +306,24 @@ __global__ void __launch_bounds__(SortCfg<K>::threads)
   const bool bulk_ok =
       ((reinterpret_cast<uintptr_t>(kin) | reinterpret_cast<uintptr_t>(vin)) & 15) == 0;
   auto is_full = [&](int64_t t) { return bulk_ok && (t + 1) * kSortTile <= n; };
+  // every digit's first output position: exclusive scan of the row totals
+  {
+    const uint32_t v = d <= mask ? rowtot[d] : 0u;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (d < kRadix && lane == 31) s_dstart[warp] = x;  // scratch until the first tile
+    __syncthreads();
+    if (d < kRadix) {
+      uint32_t pre = 0;
+      for (int w = 0; w < warp; ++w) pre += s_dstart[w];
+      s_dbase[d] = pre + x - v;
+    }
+    __syncthreads();
+  }
   // start the bulk copy of tile t into buffer b (thread 0)
   auto fetch = [&](int b, int64_t t) {
     if (t < ntiles && is_full(t)) {
@@ -278,7 +347,7 @@ __global__ void __launch_bounds__(SortCfg<K>::threads)
     const int64_t tile0 = tile * kSortTile;
     const int cnt = (int)min((int64_t)kSortTile, n - tile0);
     for (int a = threadIdx.x; a < kSortWarps * kRadix; a += kSortThreads) (&s_wcnt[0][0])[a] = 0;
-    if (d <= mask) s_base[d] = hscan[(int64_t)d * nb + tile];
+    if (d <= mask) s_base[d] = s_dbase[d] + hscan[(int64_t)d * nb + tile];
     if (threadIdx.x == 0) fetch(b ^ 1, tile + gridDim.x);
     if (is_full(tile)) {
       const uint32_t ph = (parity >> b) & 1u;
@@ -395,9 +464,7 @@ cudaError_t radix_sort_impl(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals
   constexpr int kRadix = RadixOf<K>::radix;
   uint32_t* hist = reinterpret_cast<uint32_t*>(temp);
   uint32_t* hscan = hist + nb * kRadix;
-  void* stemp = hscan + nb * kRadix;
-  unsigned long long* total = reinterpret_cast<unsigned long long*>(
-      reinterpret_cast<char*>(stemp) + scan_temp_bytes(nb * kRadix));
+  uint32_t* rowtot = hscan + nb * kRadix;  // [kRadix]
   const size_t smem = scatter_smem<K>();
   cudaError_t e =
       cudaFuncSetAttribute(k_rts_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -417,9 +484,12 @@ cudaError_t radix_sort_impl(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals
     k_rts_hist<K><<<(unsigned)nb, kSortThreads, 0, s>>>(src_k, n_cap, n_dev, shift, mask, hist, nb);
     note_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = scan_exclusive(hist, hscan, nb * (mask + 1), stemp, total, s)) != cudaSuccess) return e;
+    k_rts_rowscan<<<(unsigned)(mask + 1), kRowScanThreads, 0, s>>>(hist, hscan, nb, rowtot);
+    note_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_rts_scatter<K><<<(unsigned)grid, kSortThreads, smem, s>>>(src_k, dst_k, src_v, dst_v, n_cap,
-                                                                n_dev, shift, mask, hscan, nb, err);
+                                                                n_dev, shift, mask, hscan, rowtot, nb,
+                                                                err);
     note_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     K* tk = src_k;
@@ -469,7 +539,7 @@ template <typename K>
 size_t radix_temp_bytes_of(int64_t n) {
   const int64_t nb = (n + SortCfg<K>::tile - 1) / SortCfg<K>::tile;
   const int64_t cells = nb * RadixOf<K>::radix;
-  return (size_t)cells * 2 * sizeof(uint32_t) + scan_temp_bytes(cells) + sizeof(unsigned long long) + 256;
+  return (size_t)(cells * 2 + RadixOf<K>::radix) * sizeof(uint32_t) + 256;
 }
 
 size_t radix_temp_bytes(int64_t n, int key_bytes) {
