@@ -520,12 +520,21 @@ __device__ __forceinline__ void bin_emit_block(
   const uint32_t d_l = (kWide && units_here) ? __float_as_uint(depth[r]) : 0u;
   const int64_t s0w = s - lane;  // the warp's first item
   uint32_t carry = 0;
+  // unit u: owner lane j, row rr of its item, row mask (the next round's
+  // mask is fetched before this round's pairs are written)
+  auto unit_at = [&](int u, int& j, int& rr, unsigned long long& mask) {
+    j = unit_owner(ubase, u);
+    rr = u - __shfl_sync(0xffffffffu, ubase, j);
+    mask = u < U ? desc[s0w + j].mask[rr] : 0ull;
+  };
+  int j_nx = 0, rr_nx = 0;
+  unsigned long long mask_nx = 0ull;
+  if (U > 0) unit_at(lane, j_nx, rr_nx, mask_nx);
   for (int b = 0; b < U; b += 32) {
-    const int u = b + lane;
-    const int j = unit_owner(ubase, u);
-    const int rr = u - __shfl_sync(0xffffffffu, ubase, j);
+    const int j = j_nx, rr = rr_nx;
+    const unsigned long long mask = mask_nx;
+    if (b + 32 < U) unit_at(b + 32 + lane, j_nx, rr_nx, mask_nx);
     const unsigned long long hj = __shfl_sync(0xffffffffu, h, j);
-    const unsigned long long mask = u < U ? desc[s0w + j].mask[rr] : 0ull;
     const uint32_t c = (uint32_t)__popcll(mask);
     uint32_t incl = c;
 #pragma unroll

@@ -3,9 +3,11 @@
 // contiguous and depth-ordered; Alg. 1 stage 3).
 //
 // Radix sort: reduce-then-scan per digit (at most 8 bits for 32-bit keys, 9 for
-// 64-bit keys). Pass = (1) per-tile digit
-// histogram into a digit-major table, (2) exclusive scan of that table, which
-// yields every tile's global output base per digit, (3) stable scatter. The
+// 64-bit keys). Pass = (1) per-tile digit histogram into a digit-major table,
+// (2) per digit, the exclusive scan of its row (the tiles' counts) and the
+// row's total, one block per digit, (3) stable scatter: a tile's output base
+// for a digit is the digit's row prefix plus the scan of the row totals
+// (every scatter block scans the totals once). The
 // scatter kernel is persistent: each block walks its share of the tiles and,
 // while it ranks one tile, the bulk-copy engine (cp.async.bulk, completion on
 // an mbarrier) fetches the block's next tile into the other half of a double
