@@ -43,6 +43,23 @@ constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTMin = 1e-4f;
 
+// Hardware approximations (hand-written PTX instructions) for the staging's
+// culling bounds and skip threshold. Both only decide which list entries are
+// evaluated, never a result: the skip threshold keeps a 1e-4 margin (in log2
+// units) far above the approximation's error, and the box half-widths are
+// widened by a relative 1e-5, so no entry that can reach alpha >= 1/255 is
+// dropped and the images are the same bit for bit.
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // list entries staged per batch: one per lane (more per lane cost more shared
 // memory per warp, and fewer resident warps, than they save)
 constexpr int kNE = 1;
@@ -63,7 +80,7 @@ __host__ __device__ inline WarpSmem warp_layout(int C, int S) {
   size_t o = 0;
   w.co = o;   o += (size_t)kNB * 16;      // float4 [kNB]: scaled conic, skip threshold
   w.oc = o;   o += (size_t)3 * kNB * 8;   // float2 [3][kNB]: (opacity, colour u)
-  w.mean = o; o += (size_t)C * kNB * 8;   // float2 [C][kNB]: per-view 2D means
+  w.mean = o; o += (size_t)((C + 1) / 2) * kNB * 16;  // float4 [C/2][kNB]: means of views 2p, 2p + 1
   w.mask = o; o += (size_t)kNB * 4;       // u32 [kNB]: entry bits (set-up: key histogram)
   w.info = o; o += (size_t)S * 4;         // u32 [S]: packed subpixel (see pack_info)
   w.T = o;    o += (size_t)S * 4;         // float [S]: transmittance
@@ -196,22 +213,22 @@ __device__ __forceinline__ void warp_blend_run(const PanelGeom& g, const BlendAr
         const float4 ct = reinterpret_cast<const float4*>(a.color_tau)[rec];
         // w: log2 of the opacity ratio at which alpha reaches 1/255 (skip below)
         s_co[slot_e] = make_float4(-0.5f * kLog2e * co.x, -kLog2e * co.y, -0.5f * kLog2e * co.z,
-                                   -log2f(255.f * co.w) - 1e-4f);
+                                   -lg2_approx(255.f * co.w) - 1e-4f);
         s_oc[slot_e] = make_float2(co.w, ct.x);
         s_oc[kNB + slot_e] = make_float2(co.w, ct.y);
         s_oc[2 * kNB + slot_e] = make_float2(co.w, ct.z);
         const float det = co.x * co.z - co.y * co.y;
-        const float hx = sqrtf(fmaxf(ct.w * co.z / det, 0.f));
-        const float hy = sqrtf(fmaxf(ct.w * co.x / det, 0.f));
+        const float rdet = __fdividef(1.f, det);
+        const float hx = sqrt_approx(fmaxf(ct.w * co.z * rdet, 0.f)) * 1.00001f;
+        const float hy = sqrt_approx(fmaxf(ct.w * co.x * rdet, 0.f)) * 1.00001f;
         // a view's box [mx -+ hx] x [my -+ hy] meets a sub-box iff its mean
         // lies within these thresholds (hx, hy are shared by the cluster's
         // views): x in [ax0, ax1] left half, [ax2, ax3] right half; y alike
         const float ax0 = bx0 - hx, ax1 = bxl + hx, ax2 = bxr - hx, ax3 = bx1 + hx;
         const float ay0 = by0 - hy, ay1 = byt + hy, ay2 = byb - hy, ay3 = by1 + hy;
         const float2* mp = reinterpret_cast<const float2*>(a.means2d) + rec * C;
-        for (int l = 0; l < C; ++l) {
-          const float2 mu = mp[l];
-          s_mean[l * kNB + slot_e] = mu;
+        auto view_bits = [&](int l, float2 mu, bool store) {
+          if (store) s_mean[((l >> 1) * kNB + slot_e) * 2 + (l & 1)] = mu;
           const bool xa = mu.x >= ax0 && mu.x <= ax1;
           const bool xb = mu.x >= ax2 && mu.x <= ax3;
           const bool ya = mu.y >= ay0 && mu.y <= ay1;
@@ -225,6 +242,18 @@ __device__ __forceinline__ void warp_blend_run(const PanelGeom& g, const BlendAr
             bits = (uint32_t)(xa && ya) | ((uint32_t)(xb && ya) << 1) | ((uint32_t)(xa && yb) << 2) |
                    ((uint32_t)(xb && yb) << 3);
           mask |= bits << (l * Q);
+        };
+        if ((C & 1) == 0) {
+          // two views' means per 16-byte load
+          const float4* mp4 = reinterpret_cast<const float4*>(mp);
+          for (int l = 0; l < C; l += 2) {
+            const float4 m4 = mp4[l >> 1];
+            reinterpret_cast<float4*>(s_mean)[(l >> 1) * kNB + slot_e] = m4;
+            view_bits(l, make_float2(m4.x, m4.y), false);
+            view_bits(l + 1, make_float2(m4.z, m4.w), false);
+          }
+        } else {
+          for (int l = 0; l < C; ++l) view_bits(l, mp[l], true);
         }
       }
       if (COUNT) s_mask[slot_e] = mask;
@@ -245,7 +274,7 @@ __device__ __forceinline__ void warp_blend_run(const PanelGeom& g, const BlendAr
       const float px = (float)(x0 + xl) + 0.5f, py = (float)(y0 + yl) + 0.5f;
       ListBits bits = __shfl_sync(full, col, slot * Q + sub_of(xl, yl));
       if (!has) bits = 0;
-      const float2* mrow = s_mean + slot * kNB;
+      const float2* mrow = s_mean + (slot >> 1) * kNB * 2 + (slot & 1);  // entry g at mrow[2 g]
       const float2* orow = s_oc + u * kNB;
       int stop = -1;
       while (bits) {
@@ -256,8 +285,8 @@ __device__ __forceinline__ void warp_blend_run(const PanelGeom& g, const BlendAr
         bits &= bits - 1;
         const float4 c0 = s_co[g0];
         const float4 c1 = s_co[g1];
-        const float2 u0 = mrow[g0];
-        const float2 u1 = mrow[g1];
+        const float2 u0 = mrow[2 * g0];
+        const float2 u1 = mrow[2 * g1];
         const float p0v = quad_power(c0.x, c0.y, c0.z, px - u0.x, py - u0.y);
         const float p1v = quad_power(c1.x, c1.y, c1.z, px - u1.x, py - u1.y);
         const bool h0 = p0v <= 0.f && p0v >= c0.w;
