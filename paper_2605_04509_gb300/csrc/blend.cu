@@ -63,6 +63,7 @@ __device__ __forceinline__ float lg2_approx(float x) {
 // list entries staged per batch: one per lane (more per lane cost more shared
 // memory per warp, and fewer resident warps, than they save)
 constexpr int kNE = 1;
+static_assert(kNE == 1, "the list entry of the next batch is fetched one per lane");
 constexpr int kNB = 32 * kNE;
 typedef uint32_t ListBits;  // one list of a batch: bit e = entry e
 __device__ __forceinline__ int bits_first(ListBits b) { return __ffs(b) - 1; }
@@ -149,6 +150,12 @@ __device__ __forceinline__ void warp_blend_run(const PanelGeom& g, const BlendAr
   auto sub_of = [&](int xl, int yl) -> int {
     return (Q >= 2 && xl >= hw ? 1 : 0) + (Q == 4 && yl >= hh ? 2 : 0);
   };
+  // sub-box centres and half-widths (before the Gaussian's own half-width)
+  constexpr float kSlack = 1.f / 64.f;
+  const float cxa = 0.5f * (bx0 + bxl), rxa0 = 0.5f * (bxl - bx0) + kSlack;
+  const float cxb = 0.5f * (bxr + bx1), rxb0 = 0.5f * (bx1 - bxr) + kSlack;
+  const float cya = 0.5f * (by0 + byt), rya0 = 0.5f * (byt - by0) + kSlack;
+  const float cyb = 0.5f * (byb + by1), ryb0 = 0.5f * (by1 - byb) + kSlack;
   const uint32_t* psi_run = a.psi + (size_t)t * g.cap + s0;
   // write out subpixel id (packed inf) with its final state
   auto finish = [&](uint32_t inf, float T, float acc, uint32_t stop_at) {
@@ -197,17 +204,21 @@ __device__ __forceinline__ void warp_blend_run(const PanelGeom& g, const BlendAr
 
   int n_live = n;
   unsigned long long n_visit = 0, n_eval = 0;
+  // this lane's list entry of the next batch, fetched one batch ahead
+  uint32_t gid_next = rg.x + (uint32_t)lane < rg.y ? a.list[rg.x + lane] : 0u;
   for (uint32_t base = rg.x; base < rg.y && n_live > 0; base += kNB) {
     // stage entries base + j * 32 + lane: attributes, per-view means,
     // (view, sub-tile) bits; then lane b holds list b of the batch
     ListBits col = 0;
+    const uint32_t gid_here = gid_next;
+    if (base + kNB + (uint32_t)lane < rg.y) gid_next = a.list[base + kNB + lane];
 #pragma unroll
     for (int j = 0; j < kNE; ++j) {
       const int slot_e = j * 32 + lane;
       const uint32_t e = base + (uint32_t)slot_e;
       uint32_t mask = 0;
       if (e < rg.y) {
-        const uint32_t gid = a.list[e];
+        const uint32_t gid = gid_here;
         const size_t rec = (size_t)k * a.M + gid;
         const float4 co = reinterpret_cast<const float4*>(a.conic_opacity)[rec];
         const float4 ct = reinterpret_cast<const float4*>(a.color_tau)[rec];
@@ -224,15 +235,16 @@ __device__ __forceinline__ void warp_blend_run(const PanelGeom& g, const BlendAr
         // a view's box [mx -+ hx] x [my -+ hy] meets a sub-box iff its mean
         // lies within these thresholds (hx, hy are shared by the cluster's
         // views): x in [ax0, ax1] left half, [ax2, ax3] right half; y alike
-        const float ax0 = bx0 - hx, ax1 = bxl + hx, ax2 = bxr - hx, ax3 = bx1 + hx;
-        const float ay0 = by0 - hy, ay1 = byt + hy, ay2 = byb - hy, ay3 = by1 + hy;
+        // as centre and half-width tests |m - c| <= r (r widened by 1/64 px,
+        // above the rounding of c and of m - c on any panel of < 2^16 px)
+        const float rxa = rxa0 + hx, rxb = rxb0 + hx, rya = rya0 + hy, ryb = ryb0 + hy;
         const float2* mp = reinterpret_cast<const float2*>(a.means2d) + rec * C;
         auto view_bits = [&](int l, float2 mu, bool store) {
           if (store) s_mean[((l >> 1) * kNB + slot_e) * 2 + (l & 1)] = mu;
-          const bool xa = mu.x >= ax0 && mu.x <= ax1;
-          const bool xb = mu.x >= ax2 && mu.x <= ax3;
-          const bool ya = mu.y >= ay0 && mu.y <= ay1;
-          const bool yb = mu.y >= ay2 && mu.y <= ay3;
+          const bool xa = fabsf(mu.x - cxa) <= rxa;
+          const bool xb = fabsf(mu.x - cxb) <= rxb;
+          const bool ya = fabsf(mu.y - cya) <= rya;
+          const bool yb = fabsf(mu.y - cyb) <= ryb;
           uint32_t bits;
           if (Q == 1)
             bits = (uint32_t)(xa && ya);
