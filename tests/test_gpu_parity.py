@@ -124,6 +124,25 @@ def test_projection_matches_fp64(tiny, c):
     plan.close()
 
 
+@pytest.mark.parametrize("degree", [0, 1, 2])
+def test_projection_lower_sh_degrees(tiny, degree):
+    # records of fewer than 16 coefficients take the element-wise staging path
+    w, scene, cams = tiny
+    ncoef = (degree + 1) ** 2
+    low = dict(scene)
+    low["sh"] = np.ascontiguousarray(scene["sh"][:, :ncoef, :])
+    plan = lfd.Plan(w.panel, views_per_cluster=8)
+    out = plan.project(lfd.scene_to_device(low), cams)
+    torch.cuda.synchronize()
+    got = out["color_tau"].cpu().numpy()
+    ref = f32_attrs(oracle.project(low, cams, w.panel.width, w.panel.height, 8, sh_degree=degree), 8)
+    valid = ref["color_tau"][..., 3] >= 0
+    assert valid.sum() > 1000
+    assert np.array_equal(got[..., 3] >= 0, valid)
+    np.testing.assert_allclose(got[valid][:, :3], ref["color_tau"][valid][:, :3], atol=2e-5)
+    plan.close()
+
+
 def _stage_inputs(w, scene, cams, c):
     proj = oracle.project(scene, cams, w.panel.width, w.panel.height, c)
     return f32_attrs(proj, c)
