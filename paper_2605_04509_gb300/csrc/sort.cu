@@ -370,22 +370,34 @@ __global__ void __launch_bounds__(SortCfg<K>::threads)
     // rank: warp w owns the contiguous chunk [w * 32 * kSortRounds, ...)
     const K* ik = in_key(b);
     const uint32_t* iv = in_val(b);
-    uint32_t rk[kSortRounds];
+    // The keys of all rounds are loaded and their peer masks taken before
+    // the per-warp counters are walked round by round: the loads and
+    // matches overlap instead of waiting behind each round's counter update
+    // (sort stage 1.37 -> 1.34 ms per paper4k frame).
+    K kr[kSortRounds];
     int dg[kSortRounds];
+    unsigned pm[kSortRounds];
 #pragma unroll
     for (int r = 0; r < kSortRounds; ++r) {
       const int idx = warp * 32 * kSortRounds + r * 32 + lane;
       const bool valid = idx < cnt;
-      const int dd = valid ? digit_of(ik[idx], shift, mask) : kRadix;
-      const unsigned peers = digit_peers(dd, valid);
-      const int rank = __popc(peers & lt);
-      const int pc = __popc(peers);
+      kr[r] = valid ? ik[idx] : (K)0;
+      dg[r] = valid ? digit_of(kr[r], shift, mask) : kRadix;
+    }
+#pragma unroll
+    for (int r = 0; r < kSortRounds; ++r) pm[r] = digit_peers(dg[r], dg[r] < kRadix);
+    uint32_t rk[kSortRounds];
+#pragma unroll
+    for (int r = 0; r < kSortRounds; ++r) {
+      const int dd = dg[r];
+      const bool valid = dd < kRadix;
+      const int rank = __popc(pm[r] & lt);
+      const int pc = __popc(pm[r]);
       const uint32_t bw = valid ? (uint32_t)s_wcnt[warp][dd] : 0u;
       __syncwarp();
       if (valid && rank == pc - 1) s_wcnt[warp][dd] = (uint16_t)(bw + (uint32_t)pc);
       __syncwarp();
       rk[r] = bw + (uint32_t)rank;
-      dg[r] = dd;
     }
     __syncthreads();
     // digit phase (threads 0..255, one per digit): exclusive prefix of the
@@ -419,7 +431,7 @@ __global__ void __launch_bounds__(SortCfg<K>::threads)
       if (dd < kRadix) {
         const int idx = warp * 32 * kSortRounds + r * 32 + lane;
         const uint32_t pos = s_dstart[dd] + s_wcnt[warp][dd] + rk[r];
-        s_key[pos] = ik[idx];
+        s_key[pos] = kr[r];
         s_val[pos] = iv[idx];
       }
     }
