@@ -13,7 +13,7 @@ own stream, so that one frame's latency-bound sort overlaps the other's
 blend; every frame is the whole path. `single_stream` times the same frames
 one after the other on one stream through lfd_render. `e2e` copies the
 Gaussians in from pinned host memory and the image back, every frame, through
-the library's host-buffer entry point.
+the library's host-buffer entry point, on the same plans and streams.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -606,8 +606,6 @@ def run_ours(args):
         if rc != lfd.LFD_OK or P_f != P:
             raise RuntimeError(f"frame in flight: status {rc}, {P_f} pairs against {P}")
     in_flight_identical = all(torch.equal(o, out) for o in fouts)
-    for fp in fplans:
-        fp.close()
     del fouts
 
     frames = world * args.steps
@@ -691,9 +689,11 @@ def run_ours(args):
 
     if not args.no_e2e:
         # end to end through the host-buffer entry points: pinned Gaussians in,
-        # image out, every frame. Pipelined (lfd_render_host_async, two output
-        # buffers, one wait at the end: a frame's upload runs under the
-        # previous frame's blend) and one synchronous call per frame.
+        # image out, every frame. Pipelined: lfd_render_host_async on the F
+        # capacity-mode plans of the timed region in turn, each on its own
+        # stream (a frame's upload runs under earlier frames' work; no host
+        # read-back inside a frame), one wait per plan at the end. Beside it
+        # one synchronous lfd_render_host per frame.
         hscene = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in scene.items()}
         houts = [torch.empty((w.panel.height, w.panel.width, 3), dtype=torch.float32).pin_memory()
                  for _ in range(2)]
@@ -701,16 +701,23 @@ def run_ours(args):
             plan.render_host(hscene, cams, houts[i], stream)
         # the pipelined form allocates its second set of device buffers on
         # its first calls: warm it up too
-        for i in range(3):
-            plan.render_host_async(hscene, cams, houts[i % 2], stream)
-        plan.render_host_wait()
+        for i in range(3 * F):
+            fplans[i % F].render_host_async(hscene, cams, houts[i % 2], fstreams[i % F])
+        for fp in fplans:
+            fp.render_host_wait()
         n_e2e = max(3, min(args.steps, 10))
         barrier(world, device)
         t0 = time.perf_counter()
         for i in range(n_e2e):
-            plan.render_host_async(hscene, cams, houts[i % 2], stream)
-        plan.render_host_wait()
+            fplans[i % F].render_host_async(hscene, cams, houts[i % 2], fstreams[i % F])
+        for fp in fplans:
+            fp.render_host_wait()
         t_pipe = max_over_ranks(time.perf_counter() - t0, world, device)
+        for fp in fplans:
+            rc, P_f = fp.status_code()
+            if rc != lfd.LFD_OK or P_f != P:
+                raise RuntimeError(f"end-to-end frame: status {rc}, {P_f} pairs against {P}")
+        host_equal = all(torch.equal(h, out.cpu()) for h in houts)
         barrier(world, device)
         t0 = time.perf_counter()
         for i in range(n_e2e):
@@ -719,11 +726,15 @@ def run_ours(args):
         h2d = sum(int(v.numel() * v.element_size()) for v in hscene.values()) + cams.nbytes
         line["e2e"] = {"value": world * n_e2e / t_pipe, "unit": "frames/s",
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(houts[0].numel() * 4),
-                       "steps": n_e2e,
+                       "steps": n_e2e, "frames_in_flight": F,
+                       "host_images_equal_device_image": host_equal,
                        "api": "lfd_render_host_async per frame (pinned inputs up, image down, every "
-                              "frame), lfd_render_host_wait once at the end",
+                              "frame) on the capacity-mode plans of the timed region in turn, each "
+                              "on its own stream; lfd_render_host_wait once per plan at the end",
                        "synchronous": {"value": world * n_e2e / t_sync, "unit": "frames/s",
                                        "api": "lfd_render_host per frame (returns with the image)"}}
+    for fp in fplans:
+        fp.close()
 
     if not args.no_forms:
         line["forms"] = other_forms(args, w, scene, cams, tile, plan, out, stream, world, device,
