@@ -239,3 +239,37 @@ def test_capacity_mode_with_no_gaussians():
     img = out.cpu().numpy()
     assert np.all(img[..., 0] == np.float32(0.25)) and np.all(img[..., 2] == np.float32(0.75))
     plan.close()
+
+
+def test_frames_in_flight_on_two_plans_and_streams():
+    # the serving schedule of the benchmark: two capacity-mode plans render
+    # alternate frames on their own streams, device-resident and from pinned
+    # host buffers; every image equals the single-scene frame
+    w = synth.WORKLOADS["tiny"]
+    host = synth.scene_for(w)
+    scene = lfd.scene_to_device(host)
+    cams = synth.arc_cameras(w.rig, w.panel.width, w.panel.height)
+    ref_plan = lfd.Plan(w.panel, views_per_cluster=8)
+    want, P = reference(ref_plan, scene, cams)
+    plans = [lfd.Plan(w.panel, views_per_cluster=8) for _ in range(2)]
+    for p in plans:
+        p.reserve(scene["means"].shape[0], P + 64)
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    outs = [torch.full_like(want, -1.0) for _ in range(2)]
+    for i in range(6):
+        plans[i % 2].render(scene, cams, outs[i % 2], streams[i % 2])
+    torch.cuda.synchronize()
+    for p, o in zip(plans, outs):
+        assert p.status() == P
+        assert torch.equal(o, want)
+    hscene = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in host.items()}
+    houts = [torch.full((w.panel.height, w.panel.width, 3), -1.0).pin_memory() for _ in range(2)]
+    for i in range(6):
+        plans[i % 2].render_host_async(hscene, cams, houts[i % 2], streams[i % 2])
+    for p in plans:
+        p.render_host_wait()
+        assert p.status() == P
+    for h in houts:
+        assert torch.equal(h, want.cpu())
+    for p in plans + [ref_plan]:
+        p.close()
