@@ -44,7 +44,7 @@ WORKLOAD_TEXT = ("paper4k: 1M Gaussians (64-blob mixture, radius 10), 45 views o
                  "cone at radius 30, 3840x2160 panel, slant 0.2 rad, pitch 5.3 subpixels, "
                  "|V_k|=8 (K=6), SH degree 3, FP32")
 # tile shapes the default run's autotuner tries (paper_2605_04509_gb300.autotune)
-AUTOTUNE_TILES = ((16, 16), (24, 16), (32, 16), (32, 8))
+AUTOTUNE_TILES = ((16, 16), (24, 16), (32, 16), (32, 24), (32, 32))
 # FP32 peak of the blend's pipe: SMs (queried; 152 on GB300) x 128 FP32 lanes x
 # 2070 MHz max SM clock; the exp2 pipe's rate is taken from the probe
 FP32_LANES, SM_MAX_MHZ = 128, 2070.0

@@ -106,7 +106,7 @@ typedef struct {
   double tan_slant, pitch, k_offset;
 } lfd_panel;
 
-/* Rendering options. tile_w * tile_h <= 512, both in [4, 64]; C in
+/* Rendering options. tile_w * tile_h <= 1024, both in [4, 64]; C in
  * [1, 32] (C = 1: no attribute reuse); remap 1 = view-coherent remapping
  * (Sec. 4.3), 0 = subpixels in raster order, each thread walking its own list
  * (the ablation "w/o remap"; same image); sort_mode one of LFD_SORT_*; bg is
@@ -250,8 +250,9 @@ LFD_API int lfd_render_backward(lfd_plan *plan, const lfd_gaussians *g, const lf
  * cluster) and its own per-tile lists, one alpha per pixel for all three
  * channels, then each subpixel (x, y, u) taken from the image of its view
  * V[x, y, u] (fused into the write). Same arguments and output as
- * lfd_render; the plan's tile shape, sort mode and background apply. The
- * first call builds a one-view-per-cluster companion plan owned by this plan.
+ * lfd_render; the plan's tile shape (its height cut to 512 / tile_w for
+ * tiles of more than 512 pixels: one thread per pixel of a tile), sort mode
+ * and background apply. The first call builds a one-view-per-cluster companion plan owned by this plan.
  * Renders the same image as lfd_render with views_per_cluster = 1 (up to
  * FP32 rounding) at N x 8/3 the blend work. */
 LFD_API int lfd_render_fullframe(lfd_plan *plan, const lfd_gaussians *g, const lfd_camera *cams,

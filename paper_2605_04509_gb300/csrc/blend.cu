@@ -103,11 +103,12 @@ __device__ __forceinline__ uint32_t warp_bit_transpose(uint32_t x, int lane) {
   return x;
 }
 
-// A subpixel of a run: its position r in the run (11 bits), channel u (2),
-// local column (6) and row (6) in the tile, slot view in the cluster (5).
+// A subpixel of a run: its position r in the run (12 bits: a run holds at
+// most the 3072 subpixels of a 1024-pixel tile), channel u (2), local column
+// (6) and row (6) in the tile, slot view in the cluster (5).
 __device__ __forceinline__ uint32_t pack_info(int r, int u, int xl, int yl, int slot) {
-  return (uint32_t)r | ((uint32_t)u << 11) | ((uint32_t)xl << 13) | ((uint32_t)yl << 19) |
-         ((uint32_t)slot << 25);
+  return (uint32_t)r | ((uint32_t)u << 12) | ((uint32_t)xl << 14) | ((uint32_t)yl << 20) |
+         ((uint32_t)slot << 26);
 }
 
 // Blend of one (tile t, cluster k) run whose list is [rg.x, rg.y) by one
@@ -159,9 +160,9 @@ __device__ __forceinline__ void warp_blend_run(const PanelGeom& g, const BlendAr
   const uint32_t* psi_run = a.psi + (size_t)t * g.cap + s0;
   // write out subpixel id (packed inf) with its final state
   auto finish = [&](uint32_t inf, float T, float acc, uint32_t stop_at) {
-    const int r = (int)(inf & 2047u);
-    const int u = (int)((inf >> 11) & 3u);
-    const int x = x0 + (int)((inf >> 13) & 63u), y = y0 + (int)((inf >> 19) & 63u);
+    const int r = (int)(inf & 4095u);
+    const int u = (int)((inf >> 12) & 3u);
+    const int x = x0 + (int)((inf >> 14) & 63u), y = y0 + (int)((inf >> 20) & 63u);
     const float bg = u == 0 ? a.bg[0] : (u == 1 ? a.bg[1] : a.bg[2]);
     a.out[((int64_t)y * g.W + x) * 3 + u] = acc + T * bg;
     if (a.keep) a.keep[(size_t)t * g.cap + s0 + r] = make_uint2(stop_at, __float_as_uint(T));
@@ -280,9 +281,9 @@ __device__ __forceinline__ void warp_blend_run(const PanelGeom& g, const BlendAr
       const int id = has ? (int)s_live[p0 + lane] : 0;
       const uint32_t inf = s_info[id];
       float T = s_T[id], acc = s_acc[id];
-      const int u = (int)((inf >> 11) & 3u);
-      const int xl = (int)((inf >> 13) & 63u), yl = (int)((inf >> 19) & 63u);
-      const int slot = (int)(inf >> 25);
+      const int u = (int)((inf >> 12) & 3u);
+      const int xl = (int)((inf >> 14) & 63u), yl = (int)((inf >> 20) & 63u);
+      const int slot = (int)(inf >> 26);
       const float px = (float)(x0 + xl) + 0.5f, py = (float)(y0 + yl) + 0.5f;
       ListBits bits = __shfl_sync(full, col, slot * Q + sub_of(xl, yl));
       if (!has) bits = 0;

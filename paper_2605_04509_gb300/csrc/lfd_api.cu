@@ -343,7 +343,7 @@ int lfd_plan_create(const lfd_panel* panel, const lfd_opts* opts, lfd_plan** out
   if (P.num_views < 1 || P.num_views > kMaxViews) return fail(LFD_ERR_INVALID, "num_views not in [1, 255]");
   if (!(P.pitch > 0.0) || !isfinite(P.pitch) || !isfinite(P.tan_slant) || !isfinite(P.k_offset))
     return fail(LFD_ERR_INVALID, "pitch must be > 0 and parameters finite");
-  if (O.tile_w < 4 || O.tile_h < 4 || O.tile_w > 64 || O.tile_h > 64 || O.tile_w * O.tile_h > 512)
+  if (O.tile_w < 4 || O.tile_h < 4 || O.tile_w > 64 || O.tile_h > 64 || O.tile_w * O.tile_h > 1024)
     return fail(LFD_ERR_INVALID, "tile shape out of range");
   if (O.views_per_cluster < 1 || O.views_per_cluster > kMaxClusterViews)
     return fail(LFD_ERR_INVALID, "views_per_cluster not in [1, 32]");
@@ -890,6 +890,8 @@ int lfd_render_fullframe(lfd_plan* p, const lfd_gaussians* gs, const lfd_camera*
     lfd_opts o = p->opts;
     o.views_per_cluster = 1;
     o.remap = 1;
+    // the full-frame blend runs one thread per pixel of a tile, at most 512
+    if (o.tile_w * o.tile_h > 512) o.tile_h = 512 / o.tile_w;
     int rc = lfd_plan_create(&p->panel, &o, &p->ff_child);
     if (rc != LFD_OK) return rc;
     p->ff_child->fullframe = true;

@@ -9,7 +9,7 @@ namespace lfd {
 
 constexpr int kMaxViews = 255;
 constexpr int kMaxClusterViews = 32;
-constexpr int kMaxTileSubpixels = 3 * 512;
+constexpr int kMaxTileSubpixels = 3 * 1024;  // tiles of up to 1024 pixels
 
 // Per-launch camera table: passed by value as a kernel parameter (large
 // kernel parameters, 16 KB here), so concurrent frames never share state.

@@ -303,6 +303,27 @@ def test_without_remap_gives_the_same_image(tiny, c):
     assert torch.equal(a, b)
 
 
+def test_large_tiles_give_the_same_image(tiny):
+    # tiles of up to 1024 pixels (a run of one cluster then holds up to 3072
+    # subpixels): the image does not depend on the tile shape, and the
+    # full-frame baseline of such a plan (its tile cut to 512 pixels) neither
+    w, scene, cams = tiny
+    s = lfd.scene_to_device(scene)
+    base = lfd.Plan(w.panel, tile=(16, 16), views_per_cluster=8)
+    want, _ = base.render(s, cams)
+    want = want.clone()
+    want_ff, _ = base.render_fullframe(s, cams)
+    want_ff = want_ff.clone()
+    for tile in [(32, 24), (32, 32), (64, 16)]:
+        plan = lfd.Plan(w.panel, tile=tile, views_per_cluster=8)
+        got, _ = plan.render(s, cams)
+        assert torch.equal(got, want), tile
+        ff, _ = plan.render_fullframe(s, cams)
+        assert torch.equal(ff, want_ff), tile
+        plan.close()
+    base.close()
+
+
 def test_fullframe_baseline_matches_oracle_and_subpixel_path(tiny):
     # every view rendered whole, then interlaced: the oracle's full-frame
     # renderer, and the subpixel path with one view per cluster
@@ -440,7 +461,7 @@ def paper4k_oracle():
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("tile", [(32, 16), (16, 16)])
+@pytest.mark.parametrize("tile", [(32, 16), (16, 16), (32, 24)])
 def test_paper4k_sampled_crops(paper4k_oracle, tile):
     # The paper-scale workload at full size, in the launch configurations the
     # benchmark times (32x16 is the tile its autotuner picks); the oracle
