@@ -2,9 +2,11 @@
 
 The tile shape changes how many Gaussian-(tile, cluster) pairs the key
 generation emits and sorts (smaller tiles: more pairs, shorter lists) and how
-many subpixels one blend warp owns; it does not change the image beyond the
-FP32 rounding of the tile-bin rule (the paper gives 16x16 only as an example
-tile, Sec. 4.2). The plan's subpixels_per_thread option is still accepted as
+many subpixels one blend warp owns; it does not change the image: every
+subpixel meets the same Gaussians in the same depth order whatever the tile
+(the paper gives 16x16 only as an example tile, Sec. 4.2). Tiles may hold up
+to 1024 pixels; the default candidates span the batching range 8x8..32x16,
+and callers pass larger shapes (32x24, 32x32) where the panel favours them. The plan's subpixels_per_thread option is still accepted as
 a candidate dimension, but the warp-per-run blend ignores it, so the default
 candidate list holds only 0. The tuner renders a few frames
 with each candidate plan on the caller's scene and cameras, times them with
