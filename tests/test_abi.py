@@ -59,3 +59,25 @@ def test_null_arguments_rejected_without_gpu(lib):
     p = lfd.CPanel(100, 100, 300, 0.1, 4.0, 0.0)
     o = lfd.COpts(16, 16, 8, 1, 0, (ctypes.c_float * 3)())
     assert lib.lfd_plan_create(ctypes.byref(p), ctypes.byref(o), ctypes.byref(h)) == lfd.LFD_ERR_INVALID
+
+
+def test_tile_shape_limits_without_gpu(lib):
+    # tiles of up to 1024 pixels, each side in [4, 64]: shapes outside are
+    # rejected before any CUDA call; shapes inside pass the checks (on a
+    # machine without a GPU the plan then fails at its first allocation)
+    from paper_2605_04509_gb300 import lfd
+    p = lfd.CPanel(256, 144, 8, 0.1, 4.0, 0.0)
+    for tw, th in [(64, 17), (64, 32), (3, 16), (16, 65), (48, 24)]:
+        h = ctypes.c_void_p()
+        o = lfd.COpts(tw, th, 8, 1, 0, (ctypes.c_float * 3)())
+        assert lib.lfd_plan_create(ctypes.byref(p), ctypes.byref(o), ctypes.byref(h)) == \
+            lfd.LFD_ERR_INVALID, (tw, th)
+        assert b"tile shape" in lib.lfd_last_error()
+    for tw, th in [(32, 24), (32, 32), (64, 16), (4, 4)]:
+        h = ctypes.c_void_p()
+        o = lfd.COpts(tw, th, 8, 1, 0, (ctypes.c_float * 3)())
+        rc = lib.lfd_plan_create(ctypes.byref(p), ctypes.byref(o), ctypes.byref(h))
+        if rc == lfd.LFD_OK:
+            lib.lfd_plan_destroy(h)
+        else:
+            assert b"tile shape" not in lib.lfd_last_error(), (tw, th)
