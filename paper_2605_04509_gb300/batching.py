@@ -1,5 +1,5 @@
-"""Batched rendering of many scenes with mixed panels (the spec batching
-configuration): 16 seeded scenes (seeds 100-115) of 200k-3M Gaussians (log-
+"""Batched rendering of many scenes with mixed panels (the batching
+workload): 16 seeded scenes (seeds 100-115) of 200k-3M Gaussians (log-
 uniform), panels assigned round-robin from 1536x2048 / 48 views,
 3840x2160 / 45 views and 7680x4320 / 100 views, all attributes in FP16.
 

@@ -1,5 +1,5 @@
 """Optimisation steps through the differentiable interlaced render (the
-spec differentiation configuration): 500k Gaussians, 24 views, a
+differentiation workload): 500k Gaussians, 24 views, a
 1920x1080 panel (slant 0.2 rad, pitch 4.8 subpixels), clusters of 8 views,
 L2 loss to a target interlaced image rendered from a copy whose means are
 perturbed by N(0, 0.01) (seed 6).

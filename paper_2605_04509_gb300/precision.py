@@ -1,6 +1,5 @@
-"""FP16 / BF16 attribute storage on the precision workload (north-star
-precision configuration): 3M Gaussians, 100 views over 50 degrees, a
-7680x4320 panel (slant 0.18 rad, pitch 6.1 subpixels), clusters of 8 views.
+"""FP16 / BF16 attribute storage on the precision workload: 3M Gaussians,
+100 views over 50 degrees, a 7680x4320 panel (slant 0.18 rad, pitch 6.1 subpixels), clusters of 8 views.
 
     python -m paper_2605_04509_gb300.precision [--frames 5]
 
